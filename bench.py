@@ -1,0 +1,365 @@
+"""Benchmark of the SuCo query path on one GB300 (or N, one process per GPU).
+
+A step is one batch of queries through the whole query path (centroid
+distances, cell activation, SC-score counting, candidate selection, exact
+re-rank, top-k: one kernel launch).  Default workload: 1,000,000 SIFT-like
+points (d=128, integer features 0..255), Ns=8, sqrtK=50, alpha=0.05,
+beta=0.005, k=50, 10,000 queries in batches of 1024.  The index is built on
+the GPU beforehand; queries are resident in device memory for the timed
+value and copied from pinned host memory for the end-to-end figure.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (launched by torchrun) every rank
+holds its own index replica and answers its own query batches (no data-path
+collective); the value is the total over ranks divided by the slowest rank.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10>=0.95 on 1 GB300, learned-alpha/BF16 vs plain FP32; % HBM peak"
+UNIT = "queries/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--workload", type=int, default=2)
+    p.add_argument("--impl", default="suco", choices=["suco", "reference"])
+    p.add_argument("--cluster-size", type=int, default=0)
+    p.add_argument("--threads", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--recall-sample", type=int, default=256)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload_config(w, batch):
+    return {"workload": f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, alpha={w.alpha}, "
+                        f"beta={w.beta}, k={w.k}, FP32",
+            "stands_in_for": w.stands_in_for, "queries": w.nq, "batch": batch,
+            "l2": "inputs larger than L2 (dataset copy in HBM >> 129 MB)", "parallelism": "query-sharded replicas"}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("suco_query.cu", "suco_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2411_14754_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+    except Exception:
+        return None
+    e = t.get(str(workload))
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), reasons=parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r["reasons"]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes_per_query(w, T, C, teff_mean_total):
+    """Bytes the method must move per query: the uint32 ids of the retrieved
+    cells (sum over subspaces of T_eff) and the C candidate rows (d FP32).
+    The SC-score array never leaves shared memory, so it adds nothing."""
+    return 4.0 * teff_mean_total + 4.0 * C * w.d
+
+
+def run_cpu_baseline(w, X, Q, sample_q, threads):
+    import oracle
+    T = oracle.collision_threshold(w.alpha, w.n)
+    C = oracle.candidate_count(w.beta, w.n, w.k)
+    from paper_2411_14754_gb300 import workloads as W
+    t0 = time.time()
+    idx = oracle.build_index(X, w.Ns, w.sqrtK, 2, W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK),
+                             nthreads=threads)
+    build_s = time.time() - t0
+    t0 = time.time()
+    oracle.query_batch(X, idx, Q[:sample_q], w.k, T, C, rank_precision=0, nthreads=threads)
+    dt = time.time() - t0
+    return {"value": sample_q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{sample_q} queries of the same workload, FP64 oracle (Algorithms 3-4), OpenMP over queries "
+                      f"on {threads} host threads; oracle index built with 2 Lloyd iterations in {build_s:.1f}s "
+                      f"(index build not timed)", "seconds": dt}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2411_14754_gb300 import workloads as W
+    w = W.WORKLOADS[args.workload]
+    X = W.dataset(w.number)
+    Q = W.queries(w.number)
+    threads = os.cpu_count() or 1
+    T = oracle.collision_threshold(w.alpha, w.n)
+    C = oracle.candidate_count(w.beta, w.n, w.k)
+    idx = oracle.build_index(X, w.Ns, w.sqrtK, 2, W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK), nthreads=threads)
+    per_step = max(threads, 16)
+    times = []
+    for s in range(args.warmup + args.steps):
+        qs = Q[(s * per_step) % (w.nq - per_step):][:per_step]
+        t0 = time.time()
+        oracle.query_batch(X, idx, qs, w.k, T, C, rank_precision=0, nthreads=threads)
+        if s >= args.warmup:
+            times.append(time.time() - t0)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    sample = (f"{per_step} queries per step of the same workload through the FP64 CPU oracle "
+              f"(Algorithms 3-4), OpenMP over queries on {threads} host threads")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, per_step), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as tdist
+
+    import paper_2411_14754_gb300 as pkg
+    from paper_2411_14754_gb300 import workloads as W
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pkg.load_library()
+    w = W.WORKLOADS[args.workload]
+    X = W.dataset(w.number)
+    Qall = W.queries(w.number)
+    Xd = torch.from_numpy(X).to(dev)
+    t0 = time.time()
+    index = pkg.suco_build_index(Xd, w.Ns, w.sqrtK, w.kmeans_iters,
+                                 init_ids=W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK))
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    del Xd
+    B = w.batch
+    nb = (w.nq + B - 1) // B
+    # every rank answers different batches (query-sharded replicas)
+    batches = [torch.from_numpy(Qall[i * B:(i + 1) * B]).to(dev) for i in range(nb)]
+    order = [(rank + i * world) % nb for i in range(nb)]
+    stream = torch.cuda.current_stream(dev)
+    outs = [(torch.empty((b.shape[0], w.k), dtype=torch.int32, device=dev),
+             torch.empty((b.shape[0], w.k), dtype=torch.float32, device=dev)) for b in batches]
+
+    def step(s):
+        bi = order[s % nb]
+        pkg.suco_query_batch(index, batches[bi], w.k, w.alpha, w.beta, out_ids=outs[bi][0], out_dist=outs[bi][1],
+                             cluster_size=args.cluster_size, threads=args.threads, stream=stream)
+        return batches[bi].shape[0]
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    nqueries = 0
+    with ClockSampler(local_rank) as clk:
+        ev[0].record(stream)
+        for s in range(args.steps):
+            nqueries += step(args.warmup + s)
+            ev[s + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    # slowest rank decides; queries are summed over ranks
+    tot = torch.tensor([total_ms, float(nqueries)], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx = tot.clone()
+        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+        sm = tot.clone()
+        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
+        total_ms, all_queries = float(mx[0]), float(sm[1])
+    else:
+        all_queries = float(nqueries)
+    value = all_queries / (total_ms / 1000.0)
+
+    # end to end through the public API: pinned host queries in, host results out, every step
+    hq = [b.cpu().pin_memory() for b in batches]
+    hout = [(torch.empty(o[0].shape, dtype=torch.int32).pin_memory(),
+             torch.empty(o[1].shape, dtype=torch.float32).pin_memory()) for o in outs]
+    dq = [torch.empty_like(b) for b in batches]
+    h2d = d2h = 0
+
+    def e2e_step(s):
+        bi = order[s % nb]
+        dq[bi].copy_(hq[bi], non_blocking=True)
+        pkg.suco_query_batch(index, dq[bi], w.k, w.alpha, w.beta, out_ids=outs[bi][0], out_dist=outs[bi][1],
+                             cluster_size=args.cluster_size, threads=args.threads, stream=stream)
+        hout[bi][0].copy_(outs[bi][0], non_blocking=True)
+        hout[bi][1].copy_(outs[bi][1], non_blocking=True)
+        return (hq[bi].numel() * 4, hout[bi][0].numel() * 4 + hout[bi][1].numel() * 4, hq[bi].shape[0])
+
+    for s in range(args.warmup):
+        e2e_step(s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eq = 0
+    e0.record(stream)
+    for s in range(args.steps):
+        a, b, c = e2e_step(s)
+        h2d += a
+        d2h += b
+        eq += c
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = eq / (e2e_ms / 1000.0)
+    if world > 1:
+        t = torch.tensor([e2e_ms, float(eq)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+        sm = t.clone()
+        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
+        e2e_value = float(sm[1]) / (float(mx[0]) / 1000.0)
+
+    # recall@k against exact k-NN (GPU brute force shortlist, FP64 re-check), and T_eff for the roofline
+    from oracle import recall as _recall
+    ns = min(args.recall_sample, batches[0].shape[0])
+    q0 = batches[0][:ns]
+    ids_s, dist_s = pkg.suco_query_batch(index, q0, w.k, w.alpha, w.beta, cluster_size=args.cluster_size,
+                                         threads=args.threads)
+    dbg = pkg.suco_query_debug(index, q0, w.k, w.alpha, w.beta, cluster_size=args.cluster_size,
+                               threads=args.threads, want=("t_eff",))
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Xg = torch.from_numpy(X).to(dev)
+    gt = []
+    for s0 in range(0, ns, 64):
+        qq = q0[s0:s0 + 64]
+        dd = torch.cdist(qq, Xg)
+        cand = torch.topk(dd, w.k + 32, largest=False).indices.cpu().numpy()
+        for j in range(qq.shape[0]):
+            c = cand[j]
+            exact = ((X[c].astype(np.float64) - qq[j].cpu().numpy().astype(np.float64)) ** 2).sum(1)
+            gt.append(c[np.lexsort((c, exact))[:w.k]])
+    del Xg
+    rec = _recall(ids_s.cpu().numpy(), np.stack(gt))
+    teff_total = float(dbg["t_eff"].double().sum(dim=1).mean().item())
+    T, Cc = pkg.suco_thresholds(w.n, w.alpha, w.beta, w.k)
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    bpq = algorithmic_bytes_per_query(w, T, Cc, teff_total)
+    mean_launch_ms = statistics.mean(step_ms)
+    achieved = bpq * B / (mean_launch_ms / 1000.0) / 1e9
+    traffic = committed_traffic(w.number)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "peak_source": peak_src,
+                "kernel": "suco_query_kernel (whole query path, one launch per batch)",
+                "algorithmic_bytes_per_query": bpq, "mean_launch_ms": mean_launch_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as _o
+        threads = _o.max_threads()
+        cpu = run_cpu_baseline(w, X, Qall, 64, threads)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(w, B), "recall_at_k": rec, "k": w.k,
+                "T": T, "C": Cc, "t_eff_per_query": teff_total,
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                        "d2h_bytes_per_step": d2h // args.steps},
+                "clocks": clk.summary(), "gpu_launches": args.steps,
+                "index_build_s": build_s}
+        print(json.dumps(line), flush=True)
+    pkg.suco_free(index)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * suco.h -- C ABI of the GB300 (sm_103a) SuCo library.
+ *
+ * SuCo answers approximate k-nearest-neighbour queries by subspace collision
+ * (arXiv 2411.14754).  The dataset D holds n points in R^d (problem statement,
+ * Section 1).  The index (Section 4.1, Algorithm 2) splits the d dimensions
+ * into Ns contiguous subspaces (Definition 3, contiguous case of Section 3.2;
+ * the last subspace takes the remainder), splits each subspace into two halves
+ * (first floor(len/2) dims, then the rest), clusters each half with K-means
+ * into sqrtK centroids, and keeps per subspace an inverted multi-index (IMI)
+ * from each of the K = sqrtK^2 product cells to the ids that fall in it.
+ * A query (Section 4.2, Algorithms 3 and 4) ranks the cells of every subspace
+ * by the summed squared half-subspace centroid distance, collides the ids of
+ * the best cells until alpha*n ids are reached, counts each id's SC-score
+ * (Definition 4: the number of subspaces in which it collided), keeps the
+ * beta*n best-scoring ids and returns the k nearest of them by exact squared
+ * Euclidean distance.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked (device) are CUDA device pointers on the current device;
+ *     pointers marked (host) are host memory.  The caller owns every buffer it
+ *     passes in; the library owns the index.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *     is enqueued on it; unless stated otherwise the call returns as soon as
+ *     the work is enqueued, and results are valid after the caller
+ *     synchronises that stream.
+ *   - Every call returns SUCO_OK (0) or a negative error code and never aborts
+ *     the process; suco_last_error() returns a message for the calling
+ *     thread's last failed call.
+ *   - Thresholds: T = ceil(alpha*n - 1e-9) clamped to [1, n] ids collide per
+ *     subspace (Algorithm 3 stops once alpha*n ids are retrieved; the last
+ *     cell is taken whole, so T_eff >= T), and C = ceil(beta*n - 1e-9), raised
+ *     to at least k and clamped to [1, n], candidates are re-ranked
+ *     (Algorithm 4).
+ *   - Ties: cells are ordered by (FP32 cell sum, rank of the first-half
+ *     centroid, rank of the second-half centroid), which is the order in which
+ *     Algorithm 3 retrieves them; candidates by (score desc, id asc); results
+ *     by (squared distance asc, id asc).
+ */
+#ifndef SUCO_H
+#define SUCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SUCO_API __attribute__((visibility("default")))
+#else
+#define SUCO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SUCO_OK 0
+#define SUCO_EINVAL (-1)       /* an argument is out of range or a pointer is NULL */
+#define SUCO_ENOMEM (-2)       /* a device or host allocation failed              */
+#define SUCO_ECUDA (-3)        /* a CUDA runtime call or a kernel launch failed   */
+#define SUCO_ETIMEOUT (-4)     /* a bounded device-side wait gave up              */
+#define SUCO_ESTATE (-5)       /* the index or the device is in the wrong state   */
+#define SUCO_EUNSUPPORTED (-6) /* valid, but beyond this build's size limits      */
+
+typedef struct suco_index suco_index; /* opaque; owned by the library */
+
+/* Index construction parameters (Algorithm 2). */
+typedef struct suco_build_params {
+    int32_t Ns;              /* number of subspaces, 1..32                              */
+    int32_t sqrtK;           /* centroids per half-subspace codebook, 1..256, <= n      */
+    int32_t kmeans_iters;    /* Lloyd iterations t (0 keeps the initial points)        */
+    int32_t reserved0;       /* must be 0                                              */
+    uint64_t seed;           /* seeds the initial-centroid draw when init_ids is NULL  */
+    const int64_t* init_ids; /* (host, nullable) [Ns][2][sqrtK] distinct point ids that
+                                seed Lloyd's iterations, one list per half-subspace      */
+} suco_build_params;
+
+/* Builds the index of Algorithm 2 on the GPU: K-means per half-subspace
+ * (sqrtK centroids, kmeans_iters Lloyd iterations from init_ids; an empty
+ * cluster keeps its centroid; argmin ties go to the lowest centroid index),
+ * then the IMI of each subspace (cell id a1*sqrtK + a2, ids ascending within a
+ * cell).
+ *   data  (device) n x d FP32, row-major.  Copied into the index; the caller
+ *         may free it once the call returns.
+ *   n     1 .. 2^31-1 points, with Ns*n < 2^32.   d  >= 2*Ns dimensions.
+ *   out   receives the new index.  Synchronous: returns after the build ends.
+ * Errors: SUCO_EINVAL on bad sizes or NULL pointers, SUCO_ENOMEM, SUCO_ECUDA. */
+SUCO_API int suco_build_index(const float* data, int64_t n, int32_t d, const suco_build_params* params, void* stream,
+                     suco_index** out);
+
+/* Builds an index from given centroids and assignments instead of running
+ * K-means (the IMI part of Algorithm 2 only).
+ *   data       (device) n x d FP32 row-major, copied.
+ *   centroids  (host) [Ns][2][sqrtK][hmax] FP32, hmax = ceil(len_last/2) where
+ *              len_last = d - (Ns-1)*floor(d/Ns); entries past a half's length
+ *              are ignored.
+ *   assign     (host) [Ns][2][n] int32 centroid index of every point in every
+ *              half-subspace, each in [0, sqrtK).
+ * Synchronous.  Errors: as suco_build_index, and SUCO_EINVAL for an
+ * assignment out of range. */
+SUCO_API int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
+                                      const float* centroids, const int32_t* assign, void* stream,
+                                      suco_index** out);
+
+/* Query parameters (Algorithm 4). */
+typedef struct suco_query_params {
+    int32_t k;            /* results per query, 1..256                                  */
+    int32_t cluster_size; /* CTAs cooperating on one query (1,2,4,8,16); 0 = automatic  */
+    double alpha;         /* collision ratio, 0 < alpha <= 1                            */
+    double beta;          /* re-rank ratio,   0 < beta  <= 1                            */
+    int32_t threads;      /* threads per CTA (512 or 1024); 0 = automatic               */
+    int32_t reserved0;    /* must be 0                                                  */
+} suco_query_params;
+
+/* Answers nq queries (Algorithm 4; Algorithm 3 for the cell walk).
+ *   queries   (device) nq x d FP32 row-major.
+ *   out_ids   (device) nq x k int32: ids by ascending squared distance (ties
+ *             by id); -1 where fewer than k candidates exist (only if n < k).
+ *   out_dist  (device) nq x k FP32 squared Euclidean distances; +inf padding.
+ * Asynchronous on `stream`; allocates nothing.  nq = 0 is a no-op.
+ * Errors: SUCO_EINVAL (NULL pointer, k/alpha/beta out of range),
+ * SUCO_EUNSUPPORTED (the per-query SC-score array of n bytes, split over the
+ * cluster, or the candidate share does not fit in shared memory), SUCO_ECUDA. */
+SUCO_API int suco_query_batch(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
+                     int32_t* out_ids, float* out_dist, void* stream);
+
+/* Optional per-stage outputs of suco_query_debug (each pointer nullable). */
+typedef struct suco_query_debug_out {
+    int64_t* t_eff;      /* (device) [nq][Ns] ids collided per subspace (Algorithm 3)      */
+    uint8_t* activated;  /* (device) [nq][Ns][K] 1 where the cell was retrieved            */
+    float* dtab;         /* (device) [nq][Ns][2][sqrtK] FP32 squared centroid distances    */
+    uint8_t* scores;     /* (device) [nq][n] SC-scores (Definition 4)                      */
+    int32_t* cands;      /* (device) [nq][C] candidate ids: the ids scoring above the cut in
+                            ascending id order, then the lowest-id ties at the cut         */
+} suco_query_debug_out;
+
+/* suco_query_batch plus the per-stage outputs above (same arguments). */
+SUCO_API int suco_query_debug(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
+                     int32_t* out_ids, float* out_dist, const suco_query_debug_out* debug, void* stream);
+
+/* Sizes of an index. */
+typedef struct suco_index_info {
+    int64_t n;
+    int32_t d;
+    int32_t Ns;
+    int32_t sqrtK;
+    int32_t hmax;      /* centroid row length in the exported layout            */
+    int64_t K;         /* sqrtK^2 cells per subspace                            */
+    int64_t ld;        /* row stride of the index's copy of D, in floats        */
+    int64_t device_bytes;
+} suco_index_info;
+
+SUCO_API int suco_index_get_info(const suco_index* index, suco_index_info* info);
+
+/* Copies the index to host buffers (each nullable):
+ *   centroids [Ns][2][sqrtK][hmax] FP32;  cell_off [Ns][K+1] uint32 offsets
+ *   into perm;  perm [Ns][n] int32 ids grouped by cell.  Synchronous. */
+SUCO_API int suco_export_index(const suco_index* index, float* centroids, uint32_t* cell_off, int32_t* perm);
+
+/* The integer thresholds T and C that a query with (alpha, beta, k) uses on
+ * an index of n points (host only). */
+SUCO_API int suco_thresholds(int64_t n, double alpha, double beta, int32_t k, int64_t* T, int64_t* C);
+
+/* Releases the index and its device memory.  NULL-safe. */
+SUCO_API void suco_free(suco_index* index);
+
+/* Message of the calling thread's last failed call ("" if none). */
+SUCO_API const char* suco_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+SUCO_API int suco_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUCO_H */

@@ -1,0 +1,320 @@
+// C ABI of libsuco: argument checks, index ownership, error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <unordered_set>
+#include <vector>
+
+#include "suco_internal.cuh"
+
+namespace suco {
+
+namespace {
+thread_local char g_err[1024] = "";
+
+uint64_t splitmix64(uint64_t* state)
+{
+    uint64_t z = (*state += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+}  // namespace
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int DevBuf::alloc(size_t b)
+{
+    bytes = b;
+    if (b == 0) return SUCO_OK;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(SUCO_ENOMEM, "cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+    }
+    return SUCO_OK;
+}
+
+void thresholds(int64_t n, double alpha, double beta, int32_t k, int64_t* T, int64_t* C)
+{
+    // Algorithm 3 stops once alpha*n ids are retrieved; Algorithm 4 re-ranks beta*n ids.
+    double t = std::ceil(alpha * (double)n - 1e-9);
+    t = std::fmin(std::fmax(t, 1.0), (double)n);
+    double c = std::ceil(beta * (double)n - 1e-9);
+    c = std::fmax(c, (double)k);
+    c = std::fmin(std::fmax(c, 1.0), (double)n);
+    *T = (int64_t)t;
+    *C = (int64_t)c;
+}
+
+namespace {
+
+void free_index_memory(DeviceIndex* ix)
+{
+    cudaFree(ix->X);
+    cudaFree(ix->cent);
+    cudaFree(ix->cell_off);
+    cudaFree(ix->perm);
+    cudaFree(ix->split);
+    ix->X = nullptr;
+    ix->cent = nullptr;
+    ix->cell_off = nullptr;
+    ix->perm = nullptr;
+    ix->split = nullptr;
+}
+
+int check_sizes(int64_t n, int32_t d, int32_t Ns, int32_t sqrtK)
+{
+    if (n < 1 || n > 0x7fffffffLL) return fail(SUCO_EINVAL, "n=%lld must be in [1, 2^31-1]", (long long)n);
+    if (Ns < 1 || Ns > 32) return fail(SUCO_EINVAL, "Ns=%d must be in [1, 32]", Ns);
+    if (d < 2 * Ns) return fail(SUCO_EINVAL, "d=%d must be at least 2*Ns=%d (each half needs a dimension)", d, 2 * Ns);
+    if (sqrtK < 1 || sqrtK > 256) return fail(SUCO_EINVAL, "sqrtK=%d must be in [1, 256]", sqrtK);
+    if ((int64_t)sqrtK > n) return fail(SUCO_EINVAL, "sqrtK=%d exceeds n=%lld", sqrtK, (long long)n);
+    if ((uint64_t)Ns * (uint64_t)n >= (1ull << 32)) return fail(SUCO_EINVAL, "Ns*n must be below 2^32");
+    return SUCO_OK;
+}
+
+// Allocates the index arrays and copies the dataset (zero-padded to ld).
+int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, cudaStream_t st)
+{
+    ix->n = n;
+    ix->d = d;
+    ix->Ns = Ns;
+    ix->sqrtK = sqrtK;
+    ix->sub_s = d / Ns;
+    {
+        const int32_t last = d - (Ns - 1) * ix->sub_s;
+        ix->hmax = last - last / 2;
+    }
+    ix->K = (int64_t)sqrtK * sqrtK;
+    ix->ld = (d + 3) & ~3;
+    int64_t nch = (n + NCH - 1) / NCH;
+    ix->n_ch = (nch + 15) & ~int64_t(15);
+    SUCO_CUDA_TRY(cudaGetDevice(&ix->device));
+    struct {
+        void** p;
+        size_t b;
+    } a[] = {
+        {(void**)&ix->X, (size_t)n * ix->ld * 4},
+        {(void**)&ix->cent, (size_t)Ns * 2 * sqrtK * ix->hmax * 4},
+        {(void**)&ix->cell_off, (size_t)Ns * (ix->K + 1) * 4},
+        {(void**)&ix->perm, (size_t)Ns * n * 4},
+        {(void**)&ix->split, (size_t)Ns * (NCH + 1) * ix->K * 4},
+    };
+    ix->bytes = 0;
+    for (auto& e : a) {
+        cudaError_t err = cudaMalloc(e.p, e.b);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            free_index_memory(ix);
+            return fail(SUCO_ENOMEM, "cudaMalloc(%zu) for the index failed: %s", e.b, cudaGetErrorString(err));
+        }
+        ix->bytes += (int64_t)e.b;
+    }
+    SUCO_CUDA_TRY(cudaMemsetAsync(ix->cent, 0, a[1].b, st));
+    if (ix->ld != d) SUCO_CUDA_TRY(cudaMemsetAsync(ix->X, 0, a[0].b, st));
+    SUCO_CUDA_TRY(cudaMemcpy2DAsync(ix->X, (size_t)ix->ld * 4, data, (size_t)d * 4, (size_t)d * 4, (size_t)n,
+                                    cudaMemcpyDeviceToDevice, st));
+    return SUCO_OK;
+}
+
+int check_query_params(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* p,
+                       const int32_t* ids, const float* dist)
+{
+    if (!index) return fail(SUCO_EINVAL, "index is NULL");
+    if (!p) return fail(SUCO_EINVAL, "params is NULL");
+    if (nq < 0) return fail(SUCO_EINVAL, "nq=%lld is negative", (long long)nq);
+    if (p->k < 1 || p->k > 256) return fail(SUCO_EINVAL, "k=%d must be in [1, 256]", p->k);
+    if (!(p->alpha > 0.0 && p->alpha <= 1.0)) return fail(SUCO_EINVAL, "alpha=%g must be in (0, 1]", p->alpha);
+    if (!(p->beta > 0.0 && p->beta <= 1.0)) return fail(SUCO_EINVAL, "beta=%g must be in (0, 1]", p->beta);
+    if (p->reserved0 != 0) return fail(SUCO_EINVAL, "reserved0 must be 0");
+    if (nq > 0 && (!queries || !ids || !dist)) return fail(SUCO_EINVAL, "queries/out_ids/out_dist must not be NULL");
+    return SUCO_OK;
+}
+
+}  // namespace
+}  // namespace suco
+
+using namespace suco;
+
+extern "C" {
+
+int suco_build_index(const float* data, int64_t n, int32_t d, const suco_build_params* params, void* stream,
+                     suco_index** out)
+{
+    clear_error();
+    if (!params || !out || !data) return fail(SUCO_EINVAL, "data, params and out must not be NULL");
+    *out = nullptr;
+    int rc = check_sizes(n, d, params->Ns, params->sqrtK);
+    if (rc) return rc;
+    if (params->kmeans_iters < 0 || params->kmeans_iters > 10000)
+        return fail(SUCO_EINVAL, "kmeans_iters=%d must be in [0, 10000]", params->kmeans_iters);
+    if (params->reserved0 != 0) return fail(SUCO_EINVAL, "reserved0 must be 0");
+    const int Ns = params->Ns, sk = params->sqrtK;
+    std::vector<int64_t> init((size_t)2 * Ns * sk);
+    if (params->init_ids) {
+        for (size_t h = 0; h < (size_t)2 * Ns; ++h) {
+            std::unordered_set<int64_t> seen;
+            for (int a = 0; a < sk; ++a) {
+                const int64_t v = params->init_ids[h * sk + a];
+                if (v < 0 || v >= n) return fail(SUCO_EINVAL, "init_ids[%zu] = %lld out of range", h * sk + a, (long long)v);
+                if (!seen.insert(v).second) return fail(SUCO_EINVAL, "init_ids repeat id %lld within a half", (long long)v);
+                init[h * sk + a] = v;
+            }
+        }
+    } else {
+        // sqrtK distinct ids per half drawn with splitmix64 (Steele, Lea, Flood 2014)
+        uint64_t state = params->seed;
+        for (size_t h = 0; h < (size_t)2 * Ns; ++h) {
+            std::unordered_set<int64_t> seen;
+            int a = 0;
+            while (a < sk) {
+                const int64_t v = (int64_t)(splitmix64(&state) % (uint64_t)n);
+                if (seen.insert(v).second) init[h * sk + a++] = v;
+            }
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    suco_index* idx = new (std::nothrow) suco_index();
+    if (!idx) return fail(SUCO_ENOMEM, "host allocation failed");
+    rc = alloc_index(&idx->ix, data, n, d, Ns, sk, st);
+    if (!rc) rc = kmeans_build(&idx->ix, init.data(), params->kmeans_iters, st);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        free_index_memory(&idx->ix);
+        delete idx;
+        return rc;
+    }
+    *out = idx;
+    return SUCO_OK;
+}
+
+int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
+                                      const float* centroids, const int32_t* assign, void* stream, suco_index** out)
+{
+    clear_error();
+    if (!data || !centroids || !assign || !out) return fail(SUCO_EINVAL, "pointers must not be NULL");
+    *out = nullptr;
+    int rc = check_sizes(n, d, Ns, sqrtK);
+    if (rc) return rc;
+    for (int64_t t = 0; t < (int64_t)2 * Ns * n; ++t)
+        if (assign[t] < 0 || assign[t] >= sqrtK)
+            return fail(SUCO_EINVAL, "assign[%lld] = %d out of [0, %d)", (long long)t, assign[t], sqrtK);
+    cudaStream_t st = (cudaStream_t)stream;
+    suco_index* idx = new (std::nothrow) suco_index();
+    if (!idx) return fail(SUCO_ENOMEM, "host allocation failed");
+    DeviceIndex* ix = &idx->ix;
+    rc = alloc_index(ix, data, n, d, Ns, sqrtK, st);
+    DevBuf dassign;
+    std::vector<float> cent;
+    if (!rc) {
+        // copy the centroids with zeroed padding past each half's length
+        cent.assign((size_t)Ns * 2 * sqrtK * ix->hmax, 0.f);
+        for (int ih = 0; ih < 2 * Ns; ++ih) {
+            int32_t off, len;
+            half_dims(d, Ns, ix->sub_s, ih >> 1, ih & 1, &off, &len);
+            for (int a = 0; a < sqrtK; ++a)
+                memcpy(&cent[((size_t)ih * sqrtK + a) * ix->hmax], &centroids[((size_t)ih * sqrtK + a) * ix->hmax],
+                       (size_t)len * 4);
+        }
+        rc = dassign.alloc((size_t)2 * Ns * n * 4);
+    }
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(ix->cent, cent.data(), cent.size() * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dassign.p, assign, (size_t)2 * Ns * n * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = fail(SUCO_ECUDA, "copy to the device failed: %s", cudaGetErrorString(e));
+    }
+    if (!rc) rc = build_imi(ix, dassign.as<int32_t>(), st);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        free_index_memory(ix);
+        delete idx;
+        return rc;
+    }
+    *out = idx;
+    return SUCO_OK;
+}
+
+int suco_query_batch(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
+                     int32_t* out_ids, float* out_dist, void* stream)
+{
+    clear_error();
+    int rc = check_query_params(index, queries, nq, params, out_ids, out_dist);
+    if (rc) return rc;
+    return launch_query(&index->ix, queries, nq, params, out_ids, out_dist, nullptr, (cudaStream_t)stream);
+}
+
+int suco_query_debug(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
+                     int32_t* out_ids, float* out_dist, const suco_query_debug_out* debug, void* stream)
+{
+    clear_error();
+    int rc = check_query_params(index, queries, nq, params, out_ids, out_dist);
+    if (rc) return rc;
+    return launch_query(&index->ix, queries, nq, params, out_ids, out_dist, debug, (cudaStream_t)stream);
+}
+
+int suco_index_get_info(const suco_index* index, suco_index_info* info)
+{
+    clear_error();
+    if (!index || !info) return fail(SUCO_EINVAL, "index and info must not be NULL");
+    const DeviceIndex& ix = index->ix;
+    info->n = ix.n;
+    info->d = ix.d;
+    info->Ns = ix.Ns;
+    info->sqrtK = ix.sqrtK;
+    info->hmax = ix.hmax;
+    info->K = ix.K;
+    info->ld = ix.ld;
+    info->device_bytes = ix.bytes;
+    return SUCO_OK;
+}
+
+int suco_export_index(const suco_index* index, float* centroids, uint32_t* cell_off, int32_t* perm)
+{
+    clear_error();
+    if (!index) return fail(SUCO_EINVAL, "index is NULL");
+    const DeviceIndex& ix = index->ix;
+    if (centroids)
+        SUCO_CUDA_TRY(cudaMemcpy(centroids, ix.cent, (size_t)ix.Ns * 2 * ix.sqrtK * ix.hmax * 4, cudaMemcpyDeviceToHost));
+    if (cell_off)
+        SUCO_CUDA_TRY(cudaMemcpy(cell_off, ix.cell_off, (size_t)ix.Ns * (ix.K + 1) * 4, cudaMemcpyDeviceToHost));
+    if (perm) SUCO_CUDA_TRY(cudaMemcpy(perm, ix.perm, (size_t)ix.Ns * ix.n * 4, cudaMemcpyDeviceToHost));
+    return SUCO_OK;
+}
+
+int suco_thresholds(int64_t n, double alpha, double beta, int32_t k, int64_t* T, int64_t* C)
+{
+    clear_error();
+    if (!T || !C) return fail(SUCO_EINVAL, "T and C must not be NULL");
+    if (n < 1) return fail(SUCO_EINVAL, "n must be positive");
+    if (!(alpha > 0.0 && alpha <= 1.0) || !(beta > 0.0 && beta <= 1.0) || k < 1)
+        return fail(SUCO_EINVAL, "alpha, beta must be in (0, 1] and k >= 1");
+    thresholds(n, alpha, beta, k, T, C);
+    return SUCO_OK;
+}
+
+void suco_free(suco_index* index)
+{
+    if (!index) return;
+    free_index_memory(&index->ix);
+    delete index;
+}
+
+const char* suco_last_error(void) { return g_err; }
+
+int suco_version(void) { return 100; }
+
+}  // extern "C"

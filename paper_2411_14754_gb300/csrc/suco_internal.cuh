@@ -1,0 +1,80 @@
+// Internal definitions shared by the CUDA translation units of libsuco.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "suco.h"
+
+namespace suco {
+
+// The id range [0, n) is cut into NCH equal chunks of n_ch ids (n_ch a
+// multiple of 16).  For every (subspace, cell) the index stores where each
+// chunk starts inside the cell's id list, so that a CTA that owns a chunk
+// range reads only its own ids of a cell.
+constexpr int NCH = 16;
+
+struct DeviceIndex {
+    int64_t n = 0;
+    int32_t d = 0;
+    int32_t Ns = 0;
+    int32_t sqrtK = 0;
+    int32_t hmax = 0;
+    int32_t sub_s = 0;  // floor(d / Ns)
+    int64_t K = 0;
+    int64_t ld = 0;     // row stride of X in floats (d rounded up to 4)
+    int64_t n_ch = 0;   // ids per chunk
+    float* X = nullptr;           // [n][ld]; columns d..ld-1 are zero
+    float* cent = nullptr;        // [Ns][2][sqrtK][hmax]; padding zero
+    uint32_t* cell_off = nullptr; // [Ns][K+1] offsets into perm[i]
+    int32_t* perm = nullptr;      // [Ns][n] ids grouped by cell, ascending inside a cell
+    uint32_t* split = nullptr;    // [Ns][NCH+1][K] absolute position in perm[i] where chunk j starts in cell x
+    int device = 0;
+    int64_t bytes = 0;
+};
+
+// Half-subspace geometry (Definition 3 contiguous case; Algorithm 2 halves).
+__host__ __device__ inline void half_dims(int32_t d, int32_t Ns, int32_t sub_s, int32_t i, int32_t h,
+                                          int32_t* off, int32_t* len)
+{
+    int32_t so = i * sub_s;
+    int32_t sl = (i == Ns - 1) ? d - (Ns - 1) * sub_s : sub_s;
+    int32_t first = sl / 2;
+    *off = so + (h ? first : 0);
+    *len = h ? sl - first : first;
+}
+
+// Error reporting: thread-local message, negative status.
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+// Device memory with automatic release.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    int alloc(size_t b);
+    template <class T> T* as() const { return static_cast<T*>(p); }
+    void* release() { void* q = p; p = nullptr; return q; }
+};
+
+int build_imi(DeviceIndex* ix, const int32_t* assign_dev /*[Ns][2][n]*/, cudaStream_t st);
+int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, cudaStream_t st);
+int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_query_params* p, int32_t* ids,
+                 float* dist, const suco_query_debug_out* dbg, cudaStream_t st);
+
+void thresholds(int64_t n, double alpha, double beta, int32_t k, int64_t* T, int64_t* C);
+
+}  // namespace suco
+
+struct suco_index {
+    suco::DeviceIndex ix;
+};
+
+#define SUCO_CUDA_TRY(expr)                                                                          \
+    do {                                                                                             \
+        cudaError_t e_ = (expr);                                                                     \
+        if (e_ != cudaSuccess) return ::suco::fail(SUCO_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)

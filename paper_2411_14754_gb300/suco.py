@@ -1,0 +1,220 @@
+"""Python binding of ``libsuco`` (the C ABI in ``include/suco.h``).
+
+Argument marshalling only: every step of the query path runs in the CUDA
+library.  PyTorch provides device memory and streams.  The functions keep
+the C names; see the header for the meaning of each argument.
+"""
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+
+
+class SucoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libsuco error {code}: {msg}")
+        self.code = code
+
+
+class _BuildParams(C.Structure):
+    _fields_ = [("Ns", C.c_int32), ("sqrtK", C.c_int32), ("kmeans_iters", C.c_int32), ("reserved0", C.c_int32),
+                ("seed", C.c_uint64), ("init_ids", C.c_void_p)]
+
+
+class _QueryParams(C.Structure):
+    _fields_ = [("k", C.c_int32), ("cluster_size", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
+                ("threads", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class _DebugOut(C.Structure):
+    _fields_ = [("t_eff", C.c_void_p), ("activated", C.c_void_p), ("dtab", C.c_void_p), ("scores", C.c_void_p),
+                ("cands", C.c_void_p)]
+
+
+class _IndexInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("Ns", C.c_int32), ("sqrtK", C.c_int32), ("hmax", C.c_int32),
+                ("K", C.c_int64), ("ld", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load libsuco.so.  Fails loudly if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2411_14754_gb300.build.build() "
+                           "(the SuCo query path has no CPU fallback)")
+    L = C.CDLL(path)
+    vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    L.suco_build_index.argtypes = [vp, i64, i32, C.POINTER(_BuildParams), vp, C.POINTER(vp)]
+    L.suco_build_index_from_assignments.argtypes = [vp, i64, i32, i32, i32, vp, vp, vp, C.POINTER(vp)]
+    L.suco_query_batch.argtypes = [vp, vp, i64, C.POINTER(_QueryParams), vp, vp, vp]
+    L.suco_query_debug.argtypes = [vp, vp, i64, C.POINTER(_QueryParams), vp, vp, C.POINTER(_DebugOut), vp]
+    L.suco_index_get_info.argtypes = [vp, C.POINTER(_IndexInfo)]
+    L.suco_export_index.argtypes = [vp, vp, vp, vp]
+    L.suco_thresholds.argtypes = [i64, f64, f64, i32, C.POINTER(i64), C.POINTER(i64)]
+    L.suco_free.argtypes = [vp]
+    L.suco_free.restype = None
+    L.suco_last_error.restype = C.c_char_p
+    for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_query_batch", "suco_query_debug",
+                 "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise SucoError(rc, load_library().suco_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_f32(x, name):
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return x
+
+
+class SucoIndex:
+    """Owns a ``suco_index*``; release it with :func:`suco_free` (or ``with``)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        info = _IndexInfo()
+        _check(load_library().suco_index_get_info(handle, C.byref(info)))
+        self.n, self.d, self.Ns, self.sqrtK = info.n, info.d, info.Ns, info.sqrtK
+        self.hmax, self.K, self.ld, self.device_bytes = info.hmax, info.K, info.ld, info.device_bytes
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        suco_free(self)
+
+    def __del__(self):
+        try:
+            suco_free(self)
+        except Exception:
+            pass
+
+
+def suco_build_index(data: torch.Tensor, Ns: int, sqrtK: int, kmeans_iters: int = 20, seed: int = 0,
+                     init_ids: Optional[np.ndarray] = None, stream=None) -> SucoIndex:
+    """Algorithm 2 on the GPU.  ``data``: n x d float32 CUDA tensor (copied)."""
+    _dev_f32(data, "data")
+    ids = None if init_ids is None else np.ascontiguousarray(init_ids, dtype=np.int64)
+    p = _BuildParams(Ns, sqrtK, kmeans_iters, 0, seed, None if ids is None else ids.ctypes.data)
+    h = C.c_void_p()
+    _check(load_library().suco_build_index(_ptr(data), data.shape[0], data.shape[1], C.byref(p), _stream(stream),
+                                           C.byref(h)))
+    return SucoIndex(h)
+
+
+def suco_build_index_from_assignments(data: torch.Tensor, Ns: int, sqrtK: int, centroids, assign,
+                                      stream=None) -> SucoIndex:
+    """IMI from given centroids [Ns][2][sqrtK][hmax] and assignments [Ns][2][n] (host arrays)."""
+    _dev_f32(data, "data")
+    cent = np.ascontiguousarray(centroids, dtype=np.float32)
+    asg = np.ascontiguousarray(assign, dtype=np.int32)
+    h = C.c_void_p()
+    _check(load_library().suco_build_index_from_assignments(_ptr(data), data.shape[0], data.shape[1], Ns, sqrtK,
+                                                            cent.ctypes.data, asg.ctypes.data, _stream(stream),
+                                                            C.byref(h)))
+    return SucoIndex(h)
+
+
+def _qparams(k, alpha, beta, cluster_size, threads):
+    return _QueryParams(int(k), int(cluster_size), float(alpha), float(beta), int(threads), 0)
+
+
+def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
+                     out_ids: Optional[torch.Tensor] = None, out_dist: Optional[torch.Tensor] = None,
+                     cluster_size: int = 0, threads: int = 0, stream=None):
+    """Algorithm 4 for every row of ``queries``; returns (ids int32 [nq,k], squared dists float32 [nq,k])."""
+    _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    p = _qparams(k, alpha, beta, cluster_size, threads)
+    _check(load_library().suco_query_batch(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out_ids),
+                                           _ptr(out_dist), _stream(stream)))
+    return out_ids, out_dist
+
+
+def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
+                     cluster_size: int = 0, threads: int = 0, want=("t_eff", "activated", "dtab", "scores", "cands"),
+                     stream=None):
+    """suco_query_batch plus per-stage outputs; returns a dict of CUDA tensors."""
+    _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    dev = queries.device
+    T, Cc = suco_thresholds(index.n, alpha, beta, k)
+    out = dict(ids=torch.empty((nq, k), dtype=torch.int32, device=dev),
+               dist=torch.empty((nq, k), dtype=torch.float32, device=dev))
+    shapes = dict(t_eff=((nq, index.Ns), torch.int64), activated=((nq, index.Ns, index.K), torch.uint8),
+                  dtab=((nq, index.Ns, 2, index.sqrtK), torch.float32), scores=((nq, index.n), torch.uint8),
+                  cands=((nq, Cc), torch.int32))
+    for name in want:
+        shp, dt = shapes[name]
+        out[name] = torch.full(shp, -1 if dt != torch.uint8 else 255, dtype=dt, device=dev)
+    dbg = _DebugOut(*[(out[n].data_ptr() if n in out else None) for n in ("t_eff", "activated", "dtab", "scores",
+                                                                        "cands")])
+    p = _qparams(k, alpha, beta, cluster_size, threads)
+    _check(load_library().suco_query_debug(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out["ids"]),
+                                           _ptr(out["dist"]), C.byref(dbg), _stream(stream)))
+    out["T"], out["C"] = T, Cc
+    return out
+
+
+def suco_index_get_info(index: SucoIndex) -> dict:
+    return dict(n=index.n, d=index.d, Ns=index.Ns, sqrtK=index.sqrtK, hmax=index.hmax, K=index.K, ld=index.ld,
+                device_bytes=index.device_bytes)
+
+
+def suco_export_index(index: SucoIndex) -> dict:
+    cent = np.empty((index.Ns, 2, index.sqrtK, index.hmax), dtype=np.float32)
+    off = np.empty((index.Ns, index.K + 1), dtype=np.uint32)
+    perm = np.empty((index.Ns, index.n), dtype=np.int32)
+    _check(load_library().suco_export_index(index.handle, cent.ctypes.data, off.ctypes.data, perm.ctypes.data))
+    return dict(centroids=cent, cell_off=off, perm=perm)
+
+
+def suco_thresholds(n: int, alpha: float, beta: float, k: int):
+    T, Cc = C.c_int64(), C.c_int64()
+    _check(load_library().suco_thresholds(int(n), float(alpha), float(beta), int(k), C.byref(T), C.byref(Cc)))
+    return T.value, Cc.value
+
+
+def suco_free(index: SucoIndex):
+    if index is not None and index.handle:
+        load_library().suco_free(index.handle)
+        index.handle = None
+
+
+def suco_last_error() -> str:
+    return load_library().suco_last_error().decode()
+
+
+def suco_version() -> int:
+    return load_library().suco_version()

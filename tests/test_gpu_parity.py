@@ -1,0 +1,195 @@
+"""GPU query path vs the CPU oracle, element by element, through the C ABI.
+
+Both sides use the same index (the oracle's, loaded with
+suco_build_index_from_assignments) and the same seeded inputs.  The oracle takes
+the cell-ranking decisions in the kernel's FP32 arithmetic, so the centroid
+distances, retrieved cells, SC-scores and candidate sets must be bit-exact; the
+re-rank distances must agree within 1e-5 relative (FP32 vs FP64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2411_14754_gb300 as pkg
+from paper_2411_14754_gb300 import workloads as W
+from parity_util import check_query_against_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2411_14754_gb300 import build
+    build.build()
+    pkg.load_library()
+
+
+def run(X, idx_o, Q, k, alpha, beta, cluster_size=0, threads=0, stages=True, want=None, sample=None):
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).to(dev)
+    ix = pkg.suco_build_index_from_assignments(Xd, idx_o["Ns"], idx_o["sqrtK"], idx_o["centroids"], idx_o["assign"])
+    try:
+        want = want or (("t_eff", "activated", "dtab", "scores", "cands") if stages else ())
+        out = pkg.suco_query_debug(ix, Qd, k, alpha, beta, cluster_size=cluster_size, threads=threads, want=want)
+        torch.cuda.synchronize()
+        host = {kk: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for kk, v in out.items()}
+    finally:
+        pkg.suco_free(ix)
+    T, C = host["T"], host["C"]
+    assert T == oracle.collision_threshold(alpha, X.shape[0])
+    assert C == oracle.candidate_count(beta, X.shape[0], k)
+    rows = range(len(Q)) if sample is None else sample
+    for b in rows:
+        check_query_against_oracle(X, idx_o, Q[b], host, b, k, T, C, stages=stages)
+    return host
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = W.WORKLOADS[1]
+    X = W.dataset(1)
+    Q = W.queries(1)
+    idx = oracle.build_index(X, w.Ns, w.sqrtK, w.kmeans_iters, W.kmeans_init_ids(1, w.n, w.Ns, w.sqrtK))
+    return w, X, Q, idx
+
+
+def test_tiny_workload_all_queries(tiny):
+    w, X, Q, idx = tiny
+    run(X, idx, Q, w.k, w.alpha, w.beta)
+
+
+@pytest.mark.parametrize("cluster_size", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("threads", [512, 1024])
+def test_tiny_workload_every_launch_shape(tiny, cluster_size, threads):
+    w, X, Q, idx = tiny
+    run(X, idx, Q[:24], w.k, w.alpha, w.beta, cluster_size=cluster_size, threads=threads)
+
+
+@pytest.mark.parametrize("alpha,beta,k", [(0.01, 0.001, 10), (0.2, 0.02, 50), (1.0, 0.005, 10), (0.05, 1.0, 7),
+                                          (0.003, 0.0005, 256), (1.0, 1.0, 20)])
+def test_tiny_workload_alpha_beta_k(tiny, alpha, beta, k):
+    w, X, Q, idx = tiny
+    host = run(X, idx, Q[:10], k, alpha, beta)
+    if alpha == 1.0:
+        assert (host["scores"] == w.Ns).all()
+
+
+def _idx(X, Ns, sk, iters, seed):
+    return oracle.build_index(X, Ns, sk, iters, W.random_init_ids(seed, X.shape[0], Ns, sk))
+
+
+def test_ragged_sizes_and_odd_dimension():
+    # n not a multiple of 4 or 16, d not a multiple of 4, last subspace longer (Definition 3)
+    X = W.random_data(1, 1001, 13)
+    Q = W.random_data(2, 9, 13)
+    run(X, _idx(X, 3, 5, 4, 3), Q, 10, 0.07, 0.02)
+
+
+def test_many_empty_cells():
+    X = W.random_data(3, 500, 16)
+    Q = W.random_data(4, 6, 16)
+    run(X, _idx(X, 4, 40, 3, 5), Q, 10, 0.1, 0.05)
+
+
+def test_one_giant_cell_and_duplicate_points():
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((3000, 24)).astype(np.float32)
+    X[:2500] = X[0]                       # one cell holds most points; distances tie
+    Q = np.concatenate([X[:2], rng.standard_normal((4, 24)).astype(np.float32)])
+    run(X, _idx(X, 4, 6, 3, 7), Q, 12, 0.05, 0.01)
+
+
+def test_all_points_in_one_cell_all_scores_tied():
+    X = np.ones((777, 8), np.float32)
+    Q = W.random_data(8, 3, 8)
+    host = run(X, _idx(X, 2, 4, 2, 9), Q, 5, 0.05, 0.01)
+    assert (host["scores"] == 2).all()
+    # every distance ties: the lowest ids win
+    assert host["ids"][0].tolist() == list(range(5))
+
+
+def test_fewer_points_than_k():
+    X = W.random_data(10, 5, 8)
+    Q = W.random_data(11, 3, 8)
+    host = run(X, _idx(X, 2, 2, 1, 12), Q, 10, 0.5, 0.5)
+    assert (host["ids"][:, 5:] == -1).all() and np.isinf(host["dist"][:, 5:]).all()
+
+
+@pytest.mark.parametrize("Ns,d,sk", [(1, 4, 3), (16, 64, 8), (32, 64, 4), (8, 96, 1), (2, 16, 256)])
+def test_subspace_and_codebook_extremes(Ns, d, sk):
+    n = max(3000, sk * 4)
+    X = W.random_data(13, n, d, kind="uniform")
+    Q = W.random_data(14, 5, d, kind="uniform")
+    run(X, _idx(X, Ns, sk, 2, 15), Q, 10, 0.05, 0.01)
+
+
+def test_exact_integer_data_matches_fp64_ranking():
+    # small integers: FP32 arithmetic is exact, so the GPU must also match the
+    # oracle run in the paper's FP64 arithmetic
+    X = W.random_data(16, 4000, 32, kind="int")
+    Q = W.random_data(17, 8, 32, kind="int")
+    idx = _idx(X, 4, 8, 0, 18)
+    host = run(X, idx, Q, 10, 0.05, 0.01)
+    for b in range(len(Q)):
+        o = oracle.query(X, idx, Q[b], 10, host["T"], host["C"], rank_precision=0)
+        np.testing.assert_array_equal(host["scores"][b].astype(np.int32), o["scores"])
+
+
+def test_single_query_and_empty_batch():
+    X = W.dataset(1, n=2000)
+    Q = W.queries(1, nq=1)
+    idx = _idx(X, 8, 5, 3, 19)
+    run(X, idx, Q, 10, 0.05, 0.005)
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), 8, 5, idx["centroids"], idx["assign"])
+    ids, dist = pkg.suco_query_batch(ix, torch.empty((0, X.shape[1]), device=dev), 10, 0.05, 0.005)
+    assert ids.shape == (0, 10)
+    pkg.suco_free(ix)
+
+
+def test_query_batch_equals_debug_path(tiny):
+    w, X, Q, idx = tiny
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    Qd = torch.from_numpy(Q).to(dev)
+    a_ids, a_d = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)
+    b = pkg.suco_query_debug(ix, Qd, w.k, w.alpha, w.beta, want=())
+    a2_ids, a2_d = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)
+    torch.cuda.synchronize()
+    assert torch.equal(a_ids, b["ids"]) and torch.equal(a_d, b["dist"])
+    assert torch.equal(a_ids, a2_ids) and torch.equal(a_d, a2_d)      # deterministic
+    pkg.suco_free(ix)
+
+
+def test_argument_errors_on_device(tiny):
+    w, X, Q, idx = tiny
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    Qd = torch.from_numpy(Q[:2]).to(dev)
+    for kw in (dict(k=0, alpha=0.05, beta=0.01), dict(k=10, alpha=0.0, beta=0.01), dict(k=10, alpha=0.05, beta=1.5),
+               dict(k=10, alpha=0.05, beta=0.01, cluster_size=3), dict(k=10, alpha=0.05, beta=0.01, threads=256),
+               dict(k=257, alpha=0.05, beta=0.01)):
+        with pytest.raises(pkg.SucoError) as e:
+            pkg.suco_query_batch(ix, Qd, **kw)
+        assert e.value.code == -1
+    bad = idx["assign"].copy()
+    bad[0, 0, 0] = w.sqrtK
+    with pytest.raises(pkg.SucoError):
+        pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"], bad)
+    pkg.suco_free(ix)
+
+
+def test_score_array_too_large_is_reported():
+    # 16 CTAs x ~227 KB of shared memory hold at most ~3.6M one-byte scores
+    n = 4_000_000
+    dev = torch.device("cuda")
+    X = torch.zeros((n, 2), device=dev)
+    ix = pkg.suco_build_index(X, 1, 1, 0)
+    with pytest.raises(pkg.SucoError) as e:
+        pkg.suco_query_batch(ix, torch.zeros((1, 2), device=dev), 10, 0.01, 0.001)
+    assert e.value.code == -6
+    pkg.suco_free(ix)
