@@ -101,7 +101,7 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
     ix->K = (int64_t)sqrtK * sqrtK;
     ix->ld = (d + 3) & ~3;
     int64_t nch = (n + NCH - 1) / NCH;
-    ix->n_ch = (nch + 15) & ~int64_t(15);
+    ix->n_ch = (nch + 31) & ~int64_t(31);
     SUCO_CUDA_TRY(cudaGetDevice(&ix->device));
     struct {
         void** p;

@@ -11,7 +11,7 @@
 namespace suco {
 
 // The id range [0, n) is cut into NCH equal chunks of n_ch ids (n_ch a
-// multiple of 16).  For every (subspace, cell) the index stores where each
+// multiple of 32).  For every (subspace, cell) the index stores where each
 // chunk starts inside the cell's id list, so that a CTA that owns a chunk
 // range reads only its own ids of a cell.
 constexpr int NCH = 16;

@@ -1,31 +1,37 @@
 // The SuCo query path (Section 4.2: Algorithm 4, with Algorithm 3's cell walk)
 // as one kernel in which a thread-block cluster of CL CTAs answers one query.
 //
-// Stages inside the kernel (all in one launch, no global scratch):
+// Stages inside the kernel (one launch, no global scratch):
 //   S0  the query row is staged in shared memory.
 //   S1  squared half-subspace centroid distances d1[a], d2[c] in FP32
 //       (acc = fma(q_j - c_j, q_j - c_j, acc) over j ascending).
-//   S2  stable ranks r1[a], r2[c] of those distances (ties by centroid index).
-//   S3  cell activation: Algorithm 3 retrieves cells in ascending order of the
+//   S2  stable ranks r1[a], r2[c] of those distances (ties by centroid index)
+//       and their inverses idx1, idx2 (rank -> centroid).
+//   S3  cell activation.  Algorithm 3 retrieves cells in ascending order of the
 //       key (f32 bits of d1[a]+d2[c], r1[a], r2[c]) until alpha*n ids are
-//       collected.  Instead of walking the cells one by one, a weighted radix
-//       select over the 48-bit keys (weights = cell sizes) finds the cut key
-//       kappa* with W(key < kappa*) < T <= W(key <= kappa*); the retrieved
-//       cells are exactly those with key <= kappa*.  CTA r handles the
-//       subspaces i with i % CL == r and publishes its tables to the cluster.
-//   S4  SC-score counting (Definition 4): each CTA owns a contiguous id range
-//       and keeps one uint8 score per id in shared memory (four per 32-bit
-//       word).  It scans, for every retrieved cell of every subspace, the part
-//       of the cell's id list that falls in its range and adds 1 to the score
-//       byte with a shared-memory atomic.
-//   S5  candidate selection: counts of scores >= s are summed over the cluster
-//       through distributed shared memory; theta is the largest s with at least
-//       C scores >= s; every id above theta and the lowest-id ties at theta
-//       (up to C in total) are written, in id order, straight into the
-//       candidate slots of the CTA that will re-rank them.
+//       collected, so the retrieved cells are exactly those with key <= kappa*,
+//       where kappa* is the smallest key whose cumulative cell size reaches T.
+//       kappa* is found by a weighted histogram over linear value buckets of
+//       the cell sums (one pass over the K cells), then a weighted radix select
+//       over the few cells of the bucket that crosses T.  Because the key grows
+//       along every ranked row, the retrieved cells of a row form a prefix of
+//       that row in r2 order: the retrieved set is a "staircase", published as
+//       row prefix sums.  CTA r handles the subspaces i with i % CL == r.
+//   S4  SC-score counting (Definition 4).  Each CTA owns a contiguous id range
+//       and keeps, per subspace, one bit per id in shared memory ("collided in
+//       subspace i").  It lists its part of every retrieved cell's id list (the
+//       index's chunk splits), load-balances the flattened list over warps and
+//       sets the bits with shared-memory atomicOr.
+//   S5  candidate selection.  Bit-sliced adders turn the Ns bit planes of 32
+//       ids into their SC-scores; per-warp counts of scores >= s are summed over
+//       the cluster through distributed shared memory; theta is the largest s
+//       with at least C scores >= s; every id above theta and the lowest-id ties
+//       at theta (C in total) are written, in id order, straight into the
+//       candidate slots of the CTA that re-ranks them.
 //   S6  exact re-rank: every CTA computes FP32 squared distances of its share
-//       of the C candidates (one warp per row, float4 loads), keeps a local
-//       top-k by (distance, id), and CTA 0 merges the CL local lists.
+//       of the C candidates (one warp per row, several rows in flight per warp),
+//       keeps a local top-k by (distance, id), and CTA 0 merges the CL sorted
+//       lists by rank.
 #include <algorithm>
 #include <cstring>
 
@@ -34,8 +40,11 @@
 namespace suco {
 namespace {
 
-constexpr int MAXSEG = 4096;  // segment-list capacity per scan round
+constexpr int MAXSEG = 2048;  // retrieved-cell segments listed per scan round
 constexpr int RTILE = 2048;   // candidates per re-rank round
+constexpr int NB = 1024;      // linear value buckets of the cut search
+constexpr int MCAP = 1024;    // cells of the crossing bucket resolved from a list
+constexpr int SCAN_U = 8;     // ids in flight per lane in the scan
 
 struct QArgs {
     const float* __restrict__ X;
@@ -53,6 +62,7 @@ struct QArgs {
     int64_t nq;
     int32_t k, k_pad;
     uint32_t T, C, per_cta;
+    uint32_t span, G;  // ids per CTA, 32-id groups per CTA
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -62,7 +72,7 @@ struct QArgs {
     int32_t* dbg_cands;
     // shared-memory layout (byte offsets)
     uint32_t o_tab, tab_stride, o_q, o_hist, o_misc, o_cnt, o_seg, o_slots, o_union;
-    uint32_t score_words, sortP, mergeP;
+    uint32_t sortP, mergeP;
 };
 
 // ---------------------------------------------------------------------------
@@ -99,23 +109,9 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr)
     return v;
 }
 
-__device__ __forceinline__ unsigned long long ld_cluster_u64(uint32_t addr)
-{
-    unsigned long long v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v)
 {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t lanemask_lt()
-{
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
 }
 
 // ---------------------------------------------------------------------------
@@ -127,25 +123,33 @@ __device__ __forceinline__ unsigned long long cell_key(float a, float b, uint32_
     return ((unsigned long long)__float_as_uint(s) << 16) | (r1 << 8) | r2;
 }
 
-struct Tab {  // one subspace's ranking tables inside shared memory
+// One subspace's tables in shared memory (identical layout in every CTA).
+struct Tab {
     unsigned long long* kappa;
     unsigned long long* teff;
+    uint32_t* row_pre;  // [sqrtK+1] retrieved cells before each ranked row
     float* d1;
     float* d2;
-    uint8_t* r1;
+    uint8_t* idx1;      // rank -> centroid
+    uint8_t* idx2;
+    uint8_t* r1;        // centroid -> rank
     uint8_t* r2;
 };
 
 __device__ __forceinline__ Tab tab_at(char* smem, const QArgs& A, int i)
 {
     char* t = smem + A.o_tab + (size_t)i * A.tab_stride;
+    const int sk = A.sqrtK;
     Tab T;
     T.kappa = reinterpret_cast<unsigned long long*>(t);
     T.teff = reinterpret_cast<unsigned long long*>(t + 8);
-    T.d1 = reinterpret_cast<float*>(t + 16);
-    T.d2 = T.d1 + A.sqrtK;
-    T.r1 = reinterpret_cast<uint8_t*>(T.d2 + A.sqrtK);
-    T.r2 = T.r1 + A.sqrtK;
+    T.row_pre = reinterpret_cast<uint32_t*>(t + 16);
+    T.d1 = reinterpret_cast<float*>(t + 20 + 4 * sk);
+    T.d2 = T.d1 + sk;
+    T.idx1 = reinterpret_cast<uint8_t*>(T.d2 + sk);
+    T.idx2 = T.idx1 + sk;
+    T.r1 = T.idx2 + sk;
+    T.r2 = T.r1 + sk;
     return T;
 }
 
@@ -199,16 +203,25 @@ __device__ void block_bitonic_sort(unsigned long long* a, int P)
     }
 }
 
-// S1-S3 for subspace i of query b.
+// Value bucket of a cell sum: monotone non-decreasing in s (FP32 subtract,
+// multiply and truncation are all monotone), so bucket order respects key order.
+__device__ __forceinline__ int value_bucket(float s, float smin, float scale)
+{
+    if (!(s > smin)) return 0;
+    const float t = fminf(__fmul_rn(__fsub_rn(s, smin), scale), (float)(NB - 1));
+    return (int)t;
+}
+
+// S1-S3 for subspace i of query b (the CTA that owns i).
 template <int NT>
 __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
 {
     const int sk = A.sqrtK;
+    const int lane = threadIdx.x & 31;
     const float* qs = reinterpret_cast<const float*>(smem + A.o_q);
     Tab tb = tab_at(smem, A, i);
-    int32_t soff, slen;
-    soff = i * A.sub_s;
-    slen = (i == A.Ns - 1) ? A.d - (A.Ns - 1) * A.sub_s : A.sub_s;
+    const int soff = i * A.sub_s;
+    const int slen = (i == A.Ns - 1) ? A.d - (A.Ns - 1) * A.sub_s : A.sub_s;
     const int first = slen / 2;
     // S1: squared distances to the 2*sqrtK half-subspace centroids
     for (int t = threadIdx.x; t < 2 * sk; t += NT) {
@@ -225,7 +238,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
         (h ? tb.d2 : tb.d1)[a] = acc;
     }
     __syncthreads();
-    // S2: stable ranks
+    // S2: stable ranks and their inverses
     for (int t = threadIdx.x; t < 2 * sk; t += NT) {
         const int h = t >= sk;
         const int a = t - h * sk;
@@ -237,24 +250,110 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
             r += (w < v) || (w == v && c < a);
         }
         (h ? tb.r2 : tb.r1)[a] = (uint8_t)r;
+        (h ? tb.idx2 : tb.idx1)[r] = (uint8_t)a;
     }
     __syncthreads();
-    // S3: weighted radix select of the cut key over the K cells
-    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + A.o_hist);
+
+    // S3: the cut key kappa*
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + A.o_union);                // [NB]
+    unsigned long long* mkey = reinterpret_cast<unsigned long long*>(hist + NB);    // [MCAP]
+    uint32_t* mw = reinterpret_cast<uint32_t*>(mkey + MCAP);                        // [MCAP]
+    uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
+    uint32_t* h256 = reinterpret_cast<uint32_t*>(smem + A.o_hist);
     unsigned long long* bc = reinterpret_cast<unsigned long long*>(smem + A.o_misc);
+    uint32_t* mcount = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 10;
     const uint32_t* co = A.cell_off + (int64_t)i * (A.K + 1);
-    const int lane = threadIdx.x & 31;
-    unsigned long long prefix = 0, mask = 0, below = 0, last_w = 0;
+    const float smin = __fadd_rn(tb.d1[tb.idx1[0]], tb.d2[tb.idx2[0]]);
+    const float smax = __fadd_rn(tb.d1[tb.idx1[sk - 1]], tb.d2[tb.idx2[sk - 1]]);
+    const float range = __fsub_rn(smax, smin);
+    const float scale = range > 0.f ? __fdiv_rn((float)NB, range) : 0.f;
+    // 2-D mapping of threads onto cells: 2^lg threads per centroid row
+    int lg = 0;
+    while ((1 << lg) < sk) ++lg;
+    const int c_of = threadIdx.x & ((1 << lg) - 1);
+    const int a_of = threadIdx.x >> lg;
+    const int a_step = NT >> lg;
+
+    for (int t = threadIdx.x; t < NB; t += NT) hist[t] = 0u;
+    if (threadIdx.x == 0) *mcount = 0u;
+    __syncthreads();
+    if (c_of < sk) {
+        const float d2c = tb.d2[c_of];
+        for (int a = a_of; a < sk; a += a_step) {
+            const uint32_t x = (uint32_t)(a * sk + c_of);
+            const uint32_t w = __ldg(co + x + 1) - __ldg(co + x);
+            if (w) atomicAdd(&hist[value_bucket(__fadd_rn(tb.d1[a], d2c), smin, scale)], w);
+        }
+    }
+    __syncthreads();
+    // crossing bucket: exclusive prefix < T <= inclusive prefix
+    {
+        constexpr int BPT = NB / NT > 0 ? NB / NT : 1;
+        uint32_t v[BPT], s = 0;
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+            const int e = threadIdx.x * BPT + u;
+            v[u] = e < NB ? hist[e] : 0u;
+            s += v[u];
+        }
+        uint32_t tot;
+        uint32_t run = block_exclusive_scan<NT>(s, wtmp, &tot);
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+            const int e = threadIdx.x * BPT + u;
+            if (e < NB && run < A.T && run + v[u] >= A.T) {
+                bc[3] = (unsigned long long)e;
+                bc[4] = run;
+            }
+            run += v[u];
+        }
+    }
+    __syncthreads();
+    const int bstar = (int)bc[3];
+    unsigned long long below = bc[4];
+    // members of the crossing bucket (non-empty cells only)
+    if (c_of < sk) {
+        const float d2c = tb.d2[c_of];
+        const uint32_t r2c = tb.r2[c_of];
+        for (int a = a_of; a < sk; a += a_step) {
+            const float s = __fadd_rn(tb.d1[a], d2c);
+            if (value_bucket(s, smin, scale) != bstar) continue;
+            const uint32_t x = (uint32_t)(a * sk + c_of);
+            const uint32_t w = __ldg(co + x + 1) - __ldg(co + x);
+            if (!w) continue;
+            const uint32_t slot = atomicAdd(mcount, 1u);
+            if (slot < MCAP) {
+                mkey[slot] = ((unsigned long long)__float_as_uint(s) << 16) | ((uint32_t)tb.r1[a] << 8) | r2c;
+                mw[slot] = w;
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t nm = *mcount;
+    const bool listed = nm <= MCAP;
+    // weighted radix select of the cut key over the bucket's members
+    unsigned long long prefix = 0, mask = 0, last_w = 0;
     for (int pass = 0; pass < 6; ++pass) {
         const int shift = 40 - 8 * pass;
-        for (int t = threadIdx.x; t < 256; t += NT) hist[t] = 0u;
+        for (int t = threadIdx.x; t < 256; t += NT) h256[t] = 0u;
         __syncthreads();
-        for (int x = threadIdx.x; x < A.K; x += NT) {
-            const int a = x / sk, c = x - a * sk;
-            const unsigned long long key = cell_key(tb.d1[a], tb.d2[c], tb.r1[a], tb.r2[c]);
-            if ((key & mask) == prefix) {
+        if (listed) {
+            for (uint32_t m = threadIdx.x; m < nm; m += NT) {
+                const unsigned long long key = mkey[m];
+                if ((key & mask) == prefix) atomicAdd(&h256[(key >> shift) & 255u], mw[m]);
+            }
+        } else if (c_of < sk) {
+            const float d2c = tb.d2[c_of];
+            const uint32_t r2c = tb.r2[c_of];
+            for (int a = a_of; a < sk; a += a_step) {
+                const float s = __fadd_rn(tb.d1[a], d2c);
+                if (value_bucket(s, smin, scale) != bstar) continue;
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(s) << 16) | ((uint32_t)tb.r1[a] << 8) | r2c;
+                if ((key & mask) != prefix) continue;
+                const uint32_t x = (uint32_t)(a * sk + c_of);
                 const uint32_t w = __ldg(co + x + 1) - __ldg(co + x);
-                if (w) atomicAdd(&hist[(key >> shift) & 255u], w);
+                if (w) atomicAdd(&h256[(key >> shift) & 255u], w);
             }
         }
         __syncthreads();
@@ -263,7 +362,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
             uint32_t s = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                v[j] = hist[lane * 8 + j];
+                v[j] = h256[lane * 8 + j];
                 s += v[j];
             }
             uint32_t incl = s;
@@ -274,8 +373,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
             }
             const uint32_t excl = incl - s;
             const uint32_t need = (uint32_t)(A.T - below);
-            const bool mine = excl < need && incl >= need;
-            if (mine) {
+            if (excl < need && incl >= need) {
                 uint32_t cum = excl;
                 int bin = lane * 8 + 7;
                 uint32_t wbin = v[7];
@@ -300,11 +398,51 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
         last_w = bc[2];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        *tb.kappa = prefix;
-        *tb.teff = below + last_w;
+    // the staircase: retrieved cells of ranked row rho are its first columns in
+    // r2 order (the key grows along the row); store lengths, then prefix sums
+    for (int rho = threadIdx.x; rho < sk; rho += NT) {
+        const int a = tb.idx1[rho];
+        const float d1a = tb.d1[a];
+        int lo = 0, hi = sk;  // number of columns with key <= kappa*
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int c = tb.idx2[mid];
+            if (cell_key(d1a, tb.d2[c], (uint32_t)rho, (uint32_t)mid) <= prefix) lo = mid + 1; else hi = mid;
+        }
+        tb.row_pre[rho + 1] = (uint32_t)lo;
     }
-    if (A.dbg_teff && threadIdx.x == 0) A.dbg_teff[b * A.Ns + i] = (int64_t)(below + last_w);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr int RPL = 8;  // sqrtK <= 256 rows, 8 per lane
+        uint32_t v[RPL], s = 0;
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+            const int rho = lane * RPL + u;
+            v[u] = rho < sk ? tb.row_pre[rho + 1] : 0u;
+            s += v[u];
+        }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncwarp();
+        uint32_t run = incl - s;
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+            const int rho = lane * RPL + u;
+            if (rho < sk) tb.row_pre[rho] = run;
+            run += v[u];
+        }
+        if (lane == 31) tb.row_pre[sk] = run;
+        if (lane == 0) {
+            *tb.kappa = prefix;
+            *tb.teff = below + last_w;
+        }
+    }
+    __syncthreads();
+    if (A.dbg_teff && threadIdx.x == 0) A.dbg_teff[b * A.Ns + i] = (int64_t)*tb.teff;
     if (A.dbg_dtab)
         for (int t = threadIdx.x; t < 2 * sk; t += NT)
             A.dbg_dtab[(b * A.Ns + i) * 2 * sk + t] = t < sk ? tb.d1[t] : tb.d2[t - sk];
@@ -316,22 +454,45 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
     __syncthreads();
 }
 
-// S4 inner loop: add 1 to the score of every id in the listed segments.
+// S4 for the retrieved-cell list entries [e0, e0+m): build the segments, then
+// set the collision bits of their ids.
 template <int NT>
-__device__ void score_segments(const QArgs& A, char* smem, uint32_t m, uint32_t id0, uint32_t span)
+__device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t m, const uint32_t* sub_pre,
+                              uint32_t id0, int j0, int j1)
 {
-    uint32_t* scores = reinterpret_cast<uint32_t*>(smem + A.o_union);
+    uint32_t* planes = reinterpret_cast<uint32_t*>(smem + A.o_union);
     uint32_t* seg_start = reinterpret_cast<uint32_t*>(smem + A.o_seg);
-    uint32_t* seg_pre = seg_start + MAXSEG;
+    uint32_t* seg_plane = seg_start + MAXSEG;
+    uint32_t* seg_pre = seg_plane + MAXSEG;  // [MAXSEG+1]
     uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
-    // exclusive prefix of the segment lengths (stored in seg_pre), EPT per thread
+    const int sk = A.sqrtK;
     constexpr int EPT = MAXSEG / NT;
-    uint32_t l[EPT], s = 0;
+    uint32_t len[EPT], s = 0;
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
         const uint32_t e = threadIdx.x * EPT + u;
-        l[u] = e < m ? seg_pre[e] : 0u;
-        s += l[u];
+        len[u] = 0;
+        if (e < m) {
+            const uint32_t g = e0 + e;
+            int i = 0;
+            while (sub_pre[i + 1] <= g) ++i;
+            Tab tb = tab_at(smem, A, i);
+            const uint32_t rl = g - sub_pre[i];
+            int lo = 0, hi = sk - 1;  // last ranked row with row_pre <= rl
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tb.row_pre[mid] <= rl) lo = mid; else hi = mid - 1;
+            }
+            const uint32_t sigma = rl - tb.row_pre[lo];
+            const uint32_t cell = (uint32_t)tb.idx1[lo] * (uint32_t)sk + tb.idx2[sigma];
+            const uint32_t* sp = A.split + (int64_t)i * (NCH + 1) * A.K + cell;
+            const uint32_t s0 = __ldg(sp + (int64_t)j0 * A.K);
+            const uint32_t s1 = __ldg(sp + (int64_t)j1 * A.K);
+            len[u] = s1 - s0;
+            seg_start[e] = (uint32_t)i * (uint32_t)A.n + s0;
+            seg_plane[e] = (uint32_t)i * A.G;
+        }
+        s += len[u];
     }
     uint32_t F;
     uint32_t run = block_exclusive_scan<NT>(s, wtmp, &F);
@@ -339,115 +500,103 @@ __device__ void score_segments(const QArgs& A, char* smem, uint32_t m, uint32_t 
     for (int u = 0; u < EPT; ++u) {
         const uint32_t e = threadIdx.x * EPT + u;
         if (e < m) seg_pre[e] = run;
-        run += l[u];
+        run += len[u];
     }
     if (threadIdx.x == 0) seg_pre[m] = F;
     __syncthreads();
+    // each warp takes a contiguous share of the F ids; lanes stride by 32
     constexpr int NW = NT / 32;
-    constexpr int U = 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (uint32_t tb = (uint32_t)warp * 32 * U; tb < F; tb += NW * 32 * U) {
-        const uint32_t p0 = tb + lane;
-        int lo = 0, hi = (int)m - 1;
-        const uint32_t pp = min(p0, F - 1);
+    const uint32_t share = (F + NW - 1) / NW;
+    const uint32_t wb = min(F, (uint32_t)warp * share), we = min(F, wb + share);
+    if (wb + lane < we) {
+        uint32_t p = wb + lane;
+        int lo = 0, hi = (int)m - 1;  // last segment starting at or before p
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (seg_pre[mid] <= pp) lo = mid; else hi = mid - 1;
+            if (seg_pre[mid] <= p) lo = mid; else hi = mid - 1;
         }
         int sg = lo;
-        int32_t idv[U];
+        const uint32_t span = A.span;
+        for (; p < we; p += 32 * SCAN_U) {
+            int32_t idv[SCAN_U];
+            uint32_t pl[SCAN_U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t pu = p0 + 32 * u;
-            idv[u] = -1;
-            if (pu < F) {
-                while (seg_pre[sg + 1] <= pu) ++sg;
-                idv[u] = __ldg(A.perm + seg_start[sg] + (pu - seg_pre[sg]));
+            for (int u = 0; u < SCAN_U; ++u) {
+                const uint32_t pu = p + 32 * u;
+                idv[u] = -1;
+                pl[u] = 0;
+                if (pu < we) {
+                    while (seg_pre[sg + 1] <= pu) ++sg;
+                    idv[u] = __ldg(A.perm + seg_start[sg] + (pu - seg_pre[sg]));
+                    pl[u] = seg_plane[sg];
+                }
             }
+#pragma unroll
+            for (int u = 0; u < SCAN_U; ++u)
+                if (idv[u] >= 0) {
+                    const uint32_t loc = (uint32_t)idv[u] - id0;
+                    if (loc < span) atomicOr(&planes[pl[u] + (loc >> 5)], 1u << (loc & 31u));
+                }
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (idv[u] >= 0) {
-                const uint32_t loc = (uint32_t)idv[u] - id0;
-                if (loc < span) atomicAdd(&scores[loc >> 2], 1u << ((loc & 3u) * 8u));
-            }
     }
     __syncthreads();
 }
 
-// S4: enumerate the retrieved cells of every subspace and scan their ids.
-template <int NT>
-__device__ void count_scores(const QArgs& A, char* smem, uint32_t r)
+// Bit-sliced SC-scores of 32 ids: acc[j] holds bit j of every id's count.
+template <int NSMAX, int B>
+__device__ __forceinline__ void bitsliced_scores(const uint32_t* planes, uint32_t G, int Ns, uint32_t g,
+                                                 uint32_t acc[B])
 {
-    uint32_t* seg_start = reinterpret_cast<uint32_t*>(smem + A.o_seg);
-    uint32_t* seg_len = seg_start + MAXSEG;
-    uint32_t* misc = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 8;
-    const int sk = A.sqrtK;
-    const uint32_t id0 = r * (uint32_t)A.cpc * (uint32_t)A.n_ch;
-    const int j0 = r * A.cpc, j1 = (r + 1) * A.cpc;
-    const int total = A.Ns * A.K;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) misc[0] = 0u;
-    __syncthreads();
-    for (int g0 = 0; g0 < total; g0 += NT) {
-        const int g = g0 + threadIdx.x;
-        bool act = false;
-        uint32_t st = 0, len = 0;
-        if (g < total) {
-            const int i = g / A.K;
-            const int x = g - i * A.K;
-            Tab tb = tab_at(smem, A, i);
-            const int a = x / sk, c = x - a * sk;
-            if (cell_key(tb.d1[a], tb.d2[c], tb.r1[a], tb.r2[c]) <= *tb.kappa) {
-                const uint32_t* sp = A.split + (int64_t)i * (NCH + 1) * A.K;
-                const uint32_t s0 = __ldg(sp + (int64_t)j0 * A.K + x);
-                const uint32_t s1 = __ldg(sp + (int64_t)j1 * A.K + x);
-                len = s1 - s0;
-                st = (uint32_t)i * (uint32_t)A.n + s0;
-                act = len > 0;
+#pragma unroll
+    for (int j = 0; j < B; ++j) acc[j] = 0u;
+#pragma unroll
+    for (int i = 0; i < NSMAX; ++i) {
+        if (i < Ns) {
+            uint32_t carry = planes[(uint32_t)i * G + g];
+            // after i+1 planes a count needs at most bits(i+1) bits
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                if ((1 << j) <= i + 1) {
+                    const uint32_t t = acc[j] & carry;
+                    acc[j] ^= carry;
+                    carry = t;
+                }
             }
         }
-        const uint32_t bal = __ballot_sync(0xffffffffu, act);
-        uint32_t base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&misc[0], (uint32_t)__popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (act) {
-            const uint32_t pos = base + __popc(bal & lanemask_lt());
-            seg_start[pos] = st;
-            seg_len[pos] = len;
-        }
-        __syncthreads();
-        const uint32_t m = misc[0];
-        const bool last = g0 + NT >= total;
-        __syncthreads();
-        if (m > (uint32_t)(MAXSEG - NT) || (last && m > 0)) {
-            score_segments<NT>(A, smem, m, id0, (uint32_t)A.cpc * (uint32_t)A.n_ch);
-            if (threadIdx.x == 0) misc[0] = 0u;
-            __syncthreads();
-        }
     }
+}
+
+// Bitwise "score >= s" over the 32 ids of a bit-sliced accumulator.
+template <int B>
+__device__ __forceinline__ uint32_t bitsliced_ge(const uint32_t acc[B], uint32_t s)
+{
+    uint32_t ge = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < B; ++j) ge = ((s >> j) & 1u) ? (acc[j] & ge) : (acc[j] | ge);
+    if (s >> B) ge = 0u;
+    return ge;
 }
 
 template <int NT, int NSMAX>
 __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
 {
     extern __shared__ __align__(16) char smem[];
+    constexpr int B = NSMAX == 8 ? 4 : (NSMAX == 16 ? 5 : 6);
+    constexpr int NW = NT / 32;
+    constexpr int NC = NSMAX + 2;  // count slots: [0] = valid ids, [s] = #scores >= s
     const uint32_t r = cluster_rank();
     const int CL = A.CL;
     const int64_t b = blockIdx.x / CL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = NT / 32;
 
-    // ---- S0: stage the query, clear the score array and the published counts
+    // ---- S0: stage the query; clear the published counts and candidate slots
     {
         float* qs = reinterpret_cast<float*>(smem + A.o_q);
         const float* qg = A.Q + b * A.d;
         for (int j = threadIdx.x; j < A.ld; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
-        uint4* sw = reinterpret_cast<uint4*>(smem + A.o_union);
-        const uint4 z = make_uint4(0, 0, 0, 0);
-        for (uint32_t w = threadIdx.x; w < A.score_words / 4; w += NT) sw[w] = z;
         uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);
-        for (int t = threadIdx.x; t < NSMAX + 2; t += NT) cnt[t] = 0u;
+        for (int t = threadIdx.x; t < NC; t += NT) cnt[t] = 0u;
         uint32_t* sl = reinterpret_cast<uint32_t*>(smem + A.o_slots);
         for (uint32_t t = threadIdx.x; t < A.per_cta; t += NT) sl[t] = 0xffffffffu;
     }
@@ -455,9 +604,16 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
 
     // ---- S1-S3 for the subspaces this CTA owns
     for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT>(A, smem, b, i);
-    cluster_sync();  // #1: every subspace's cut key is published
+    // clear the bit planes (the union region served as S3 scratch)
+    {
+        uint4* pw = reinterpret_cast<uint4*>(smem + A.o_union);
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        const uint32_t n16 = ((uint32_t)A.Ns * A.G + 3) / 4;  // the union region is a multiple of 16 bytes
+        for (uint32_t w = threadIdx.x; w < n16; w += NT) pw[w] = z;
+    }
+    cluster_sync();  // #1: every subspace's cut and staircase are published
 
-    // ---- gather the other CTAs' tables
+    // ---- copy the other CTAs' tables
     {
         const uint32_t words = A.tab_stride / 4;
         for (uint32_t t = threadIdx.x; t < (uint32_t)A.Ns * words; t += NT) {
@@ -470,53 +626,82 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
     }
     __syncthreads();
 
-    // ---- S4: SC-score counting over this CTA's id range
-    count_scores<NT>(A, smem, r);
-    const uint32_t id0 = r * (uint32_t)A.cpc * (uint32_t)A.n_ch;
-    const uint32_t span = (uint32_t)A.cpc * (uint32_t)A.n_ch;
-    const uint32_t valid = id0 >= A.n ? 0u : (uint32_t)min((int64_t)span, A.n - (int64_t)id0);
-    const uint32_t* scores = reinterpret_cast<const uint32_t*>(smem + A.o_union);
-    const uint32_t nwords = (valid + 3) / 4;
-    if (A.dbg_scores)
-        for (uint32_t j = threadIdx.x; j < valid; j += NT)
-            A.dbg_scores[b * A.n + id0 + j] = (uint8_t)(scores[j >> 2] >> ((j & 3) * 8));
+    // ---- S4: set the collision bits of this CTA's id range
+    const uint32_t id0 = r * A.span;
+    const int j0 = r * A.cpc, j1 = (r + 1) * A.cpc;
+    uint32_t* sub_pre = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 32;  // [Ns+1]
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int i = 0; i < A.Ns; ++i) {
+            sub_pre[i] = acc;
+            acc += tab_at(smem, A, i).row_pre[A.sqrtK];
+        }
+        sub_pre[A.Ns] = acc;
+    }
+    __syncthreads();
+    const uint32_t L = sub_pre[A.Ns];
+    for (uint32_t e0 = 0; e0 < L; e0 += MAXSEG)
+        scan_segments<NT>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, id0, j0, j1);
 
-    // ---- S5: cluster-wide score histogram, cut, and candidate hand-off
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);  // [0] = valid ids, [s] = #scores >= s
+    const uint32_t* planes = reinterpret_cast<const uint32_t*>(smem + A.o_union);
+    const uint32_t valid = id0 >= A.n ? 0u : (uint32_t)min((int64_t)A.span, A.n - (int64_t)id0);
+    if (A.dbg_scores)
+        for (uint32_t j = threadIdx.x; j < valid; j += NT) {
+            uint32_t sc = 0;
+            for (int i = 0; i < A.Ns; ++i) sc += (planes[(uint32_t)i * A.G + (j >> 5)] >> (j & 31)) & 1u;
+            A.dbg_scores[b * A.n + id0 + j] = (uint8_t)sc;
+        }
+
+    // ---- S5: counts of scores >= s per warp range, the cut theta, hand-off
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);  // this CTA's published counts [NC]
+    uint32_t* allc = cnt + NC;                                     // [CL][NC]
+    uint32_t* wcnt = allc + CL * NC;                               // [NW][NC]
+    const uint32_t ngroups = (valid + 31) / 32;
+    const uint32_t gpw = (ngroups + NW - 1) / NW;
+    const uint32_t gb = min(ngroups, (uint32_t)warp * gpw), ge = min(ngroups, gb + gpw);
     {
         uint32_t c[NSMAX];
 #pragma unroll
         for (int s = 0; s < NSMAX; ++s) c[s] = 0u;
-        for (uint32_t w = threadIdx.x; w < nwords; w += NT) {
-            const uint32_t v = scores[w];
+        for (uint32_t g = gb + lane; g < ge; g += 32) {
+            uint32_t acc[B];
+            bitsliced_scores<NSMAX, B>(planes, A.G, A.Ns, g, acc);
 #pragma unroll
-            for (int s = 0; s < NSMAX; ++s) c[s] += __popc(__vcmpgeu4(v, (uint32_t)(s + 1) * 0x01010101u)) >> 3;
+            for (int s = 0; s < NSMAX; ++s)
+                if (s < A.Ns) c[s] += __popc(bitsliced_ge<B>(acc, (uint32_t)(s + 1)));
         }
 #pragma unroll
         for (int s = 0; s < NSMAX; ++s) {
             uint32_t v = c[s];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && v) atomicAdd(&cnt[s + 1], v);
+            if (lane == 0) {
+                wcnt[warp * NC + s + 1] = v;
+                if (v) atomicAdd(&cnt[s + 1], v);
+            }
+        }
+        if (lane == 0) {
+            const uint32_t lo = gb * 32, hi = min(valid, ge * 32);
+            wcnt[warp * NC] = hi > lo ? hi - lo : 0u;
+            wcnt[warp * NC + NSMAX + 1] = 0u;
         }
         if (threadIdx.x == 0) cnt[0] = valid;
     }
     cluster_sync();  // #2: every CTA's counts are published
-    uint32_t* allc = cnt + (NSMAX + 2);                              // [CL][NSMAX+2]
-    uint32_t* sel = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 16;  // theta, n_gt, need_eq, gt_pre, eq_pre
-    uint32_t* slot_base = sel + 8;                                    // [CL] remote slot addresses
-    for (int t = threadIdx.x; t < CL * (NSMAX + 2); t += NT) {
-        const int rr = t / (NSMAX + 2), s = t - rr * (NSMAX + 2);
+    uint32_t* sel = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 72;  // theta, n_gt, need_eq
+    uint32_t* slot_base = sel + 8;                                      // [CL] remote slot addresses
+    uint32_t* wbase = reinterpret_cast<uint32_t*>(smem + A.o_hist);     // [NW][2] per-warp output bases
+    for (int t = threadIdx.x; t < CL * NC; t += NT) {
+        const int rr = t / NC, s = t - rr * NC;
         allc[t] = ld_cluster_u32(map_rank(smem_addr(cnt + s), (uint32_t)rr));
     }
-    for (int t = threadIdx.x; t < CL; t += NT)
-        slot_base[t] = map_rank(smem_addr(smem + A.o_slots), (uint32_t)t);
+    for (int t = threadIdx.x; t < CL; t += NT) slot_base[t] = map_rank(smem_addr(smem + A.o_slots), (uint32_t)t);
     __syncthreads();
     if (threadIdx.x == 0) {
         int theta = 0;
         for (int s = A.Ns; s >= 1; --s) {
             uint32_t tot = 0;
-            for (int rr = 0; rr < CL; ++rr) tot += allc[rr * (NSMAX + 2) + s];
+            for (int rr = 0; rr < CL; ++rr) tot += allc[rr * NC + s];
             if (tot >= A.C) {
                 theta = s;
                 break;
@@ -524,7 +709,7 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
         }
         uint32_t n_gt = 0, gt_pre = 0, eq_pre = 0;
         for (int rr = 0; rr < CL; ++rr) {
-            const uint32_t* cr = allc + rr * (NSMAX + 2);
+            const uint32_t* cr = allc + rr * NC;
             const uint32_t gt = cr[theta + 1];
             const uint32_t eq = cr[theta] - gt;
             n_gt += gt;
@@ -533,61 +718,42 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
                 eq_pre += eq;
             }
         }
+        // per-warp output bases, warps in id order
+        uint32_t sg = gt_pre, se = eq_pre;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t gt = wcnt[w * NC + theta + 1];
+            const uint32_t eq = wcnt[w * NC + theta] - gt;
+            wbase[2 * w] = sg;
+            wbase[2 * w + 1] = se;
+            sg += gt;
+            se += eq;
+        }
         sel[0] = (uint32_t)theta;
         sel[1] = n_gt;
         sel[2] = A.C - n_gt;
-        sel[3] = gt_pre;
-        sel[4] = eq_pre;
     }
     __syncthreads();
     {
         const uint32_t theta = sel[0], n_gt = sel[1], need_eq = sel[2];
-        const uint32_t th4 = theta * 0x01010101u;
-        const uint32_t wpw = (nwords + NW - 1) / NW;
-        const uint32_t wb = min(nwords, (uint32_t)warp * wpw), we = min(nwords, wb + wpw);
-        uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist);  // [0,NW) gt, [64,64+NW) eq
-        // pass 1: per-warp counts
-        uint32_t g = 0, e = 0;
-        for (uint32_t w = wb + lane; w < we; w += 32) {
-            const uint32_t v = scores[w];
-            uint32_t em = __vcmpeq4(v, th4);
-            if (4 * w + 4 > valid) em &= (1u << (8 * (valid - 4 * w))) - 1u;
-            g += __popc(__vcmpgtu4(v, th4)) >> 3;
-            e += __popc(em) >> 3;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            g += __shfl_xor_sync(0xffffffffu, g, o);
-            e += __shfl_xor_sync(0xffffffffu, e, o);
-        }
-        if (lane == 0) {
-            wtmp[warp] = g;
-            wtmp[64 + warp] = e;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t sg = sel[3], se = sel[4];
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t tg = wtmp[w], te = wtmp[64 + w];
-                wtmp[w] = sg;
-                wtmp[64 + w] = se;
-                sg += tg;
-                se += te;
-            }
-        }
-        __syncthreads();
-        // pass 2: hand each selected id to the CTA that re-ranks its position
-        uint32_t gb = wtmp[warp], eb = wtmp[64 + warp];
-        for (uint32_t w0 = wb; w0 < we; w0 += 32) {
-            const uint32_t w = w0 + lane;
+        uint32_t pgb = wbase[2 * warp], peb = wbase[2 * warp + 1];
+        for (uint32_t g0 = gb; g0 < ge; g0 += 32) {
+            const bool want_eq = peb < need_eq;
+            const uint32_t g = g0 + lane;
             uint32_t gm = 0, em = 0;
-            if (w < we) {
-                const uint32_t v = scores[w];
-                gm = __vcmpgtu4(v, th4);
-                em = __vcmpeq4(v, th4);
-                if (4 * w + 4 > valid) em &= (1u << (8 * (valid - 4 * w))) - 1u;
+            if (g < ge) {
+                uint32_t acc[B];
+                bitsliced_scores<NSMAX, B>(planes, A.G, A.Ns, g, acc);
+                gm = bitsliced_ge<B>(acc, theta + 1);
+                em = bitsliced_ge<B>(acc, theta) & ~gm;
+                const uint32_t base = g * 32;
+                if (base + 32 > valid) em &= valid > base ? (0xffffffffu >> (32 - (valid - base))) : 0u;
             }
-            const uint32_t cg = __popc(gm) >> 3, ce = __popc(em) >> 3;
+            const uint32_t cg = __popc(gm), ce = __popc(em);
+            const uint32_t any = __ballot_sync(0xffffffffu, (gm | (want_eq ? em : 0u)) != 0u);
+            if (!any) {
+                if (want_eq) peb += __reduce_add_sync(0xffffffffu, ce);
+                continue;
+            }
             uint32_t ig = cg, ie = ce;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -598,28 +764,32 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
                     ie += ye;
                 }
             }
-            uint32_t pg = gb + ig - cg, pe = eb + ie - ce;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t id = id0 + 4 * w + j;
+            uint32_t pg = pgb + ig - cg, pe = peb + ie - ce;
+            const uint32_t base_id = id0 + g * 32;
+            while (gm | em) {
+                const int j = __ffs(gm | em) - 1;
+                const uint32_t bit = 1u << j;
                 uint32_t pos = 0xffffffffu;
-                if ((gm >> (8 * j)) & 1u) {
+                if (gm & bit) {
                     pos = pg++;
-                } else if ((em >> (8 * j)) & 1u) {
+                } else {
                     if (pe < need_eq) pos = n_gt + pe;
                     ++pe;
                 }
+                gm &= ~bit;
+                em &= ~bit;
                 if (pos != 0xffffffffu) {
                     const uint32_t owner = pos / A.per_cta;
+                    const uint32_t id = base_id + (uint32_t)j;
                     st_cluster_u32(slot_base[owner] + 4u * (pos - owner * A.per_cta), id);
                     if (A.dbg_cands) A.dbg_cands[b * A.C + pos] = (int32_t)id;
                 }
             }
-            gb += __shfl_sync(0xffffffffu, ig, 31);
-            eb += __shfl_sync(0xffffffffu, ie, 31);
+            pgb += __shfl_sync(0xffffffffu, ig, 31);
+            peb += __shfl_sync(0xffffffffu, ie, 31);
         }
     }
-    cluster_sync();  // #3: every candidate slot is filled; scores are dead
+    cluster_sync();  // #3: every candidate slot is filled; the bit planes are dead
 
     // ---- S6: exact FP32 re-rank of this CTA's share of the candidates
     unsigned long long* topk = reinterpret_cast<unsigned long long*>(smem + A.o_union);
@@ -628,28 +798,29 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
     const uint32_t mine = A.C > r * A.per_cta ? min(A.per_cta, A.C - r * A.per_cta) : 0u;
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
     const int ld4 = (int)(A.ld / 4);
+    constexpr int RW = NT == 1024 ? 4 : 8;  // rows in flight per warp (register budget)
     uint32_t kc = 0;
     for (uint32_t t0 = 0; t0 < mine; t0 += RTILE) {
         const uint32_t tc = min((uint32_t)RTILE, mine - t0);
         for (uint32_t t = threadIdx.x; t < (uint32_t)A.sortP; t += NT)
             if (t < kc) sortbuf[t] = topk[t]; else if (t >= kc + tc) sortbuf[t] = ~0ull;
-        for (uint32_t j = (uint32_t)warp * 4; j < tc; j += NW * 4) {
-            int32_t id[4];
-            float acc[4];
+        for (uint32_t j = (uint32_t)warp * RW; j < tc; j += NW * RW) {
+            int32_t id[RW];
+            float acc[RW];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < RW; ++u) {
                 const uint32_t sv = j + u < tc ? slots[t0 + j + u] : 0xffffffffu;
                 id[u] = sv < (uint32_t)A.n ? (int32_t)sv : -1;
                 acc[u] = 0.f;
             }
             for (int c = lane; c < ld4; c += 32) {
                 const float4 qv = q4[c];
-                float4 xv[4];
+                float4 xv[RW];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < RW; ++u)
                     if (id[u] >= 0) xv[u] = __ldg(reinterpret_cast<const float4*>(A.X + (int64_t)id[u] * A.ld) + c);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < RW; ++u)
                     if (id[u] >= 0) {
                         float df = __fsub_rn(xv[u].x, qv.x);
                         acc[u] = __fmaf_rn(df, df, acc[u]);
@@ -662,7 +833,7 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
                     }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < RW; ++u) {
                 float v = acc[u];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -678,25 +849,56 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
         __syncthreads();
     }
     for (uint32_t t = kc + threadIdx.x; t < (uint32_t)A.k; t += NT) topk[t] = ~0ull;
-    cluster_sync();  // #4: every local top-k is published
+    cluster_sync();  // #4: every local top-k is published (sorted, padded to k)
 
     if (r == 0) {
+        // merge by rank: a key's final position is the number of smaller keys
+        // over all CL sorted lists (keys are unique because ids are)
         const uint32_t tot = (uint32_t)CL * A.k;
-        for (uint32_t t = threadIdx.x; t < (uint32_t)A.mergeP; t += NT) {
-            unsigned long long v = ~0ull;
-            if (t < tot) {
-                const uint32_t rr = t / A.k, e = t - rr * A.k;
-                v = rr == 0 ? topk[e] : ld_cluster_u64(map_rank(smem_addr(topk + e), rr));
+        unsigned long long* all = sortbuf;
+        for (uint32_t t = threadIdx.x; t < tot; t += NT) {
+            const uint32_t rr = t / A.k, e = t - rr * A.k;
+            unsigned long long v;
+            if (rr == 0) {
+                v = topk[e];
+            } else {
+                const uint32_t ad = map_rank(smem_addr(topk + e), rr);
+                const uint32_t lo = ld_cluster_u32(ad), hi = ld_cluster_u32(ad + 4);
+                v = ((unsigned long long)hi << 32) | lo;
             }
-            sortbuf[t] = v;
+            all[t] = v;
         }
+        uint32_t* nreal = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 96;
+        if (threadIdx.x == 0) *nreal = 0u;
         __syncthreads();
-        block_bitonic_sort<NT>(sortbuf, (int)A.mergeP);
-        for (int t = threadIdx.x; t < A.k; t += NT) {
-            const unsigned long long v = sortbuf[t];
-            const bool pad = v == ~0ull;
-            A.out_ids[b * A.k + t] = pad ? -1 : (int32_t)(uint32_t)(v & 0xffffffffu);
-            A.out_dist[b * A.k + t] = pad ? __int_as_float(0x7f800000) : __uint_as_float((uint32_t)(v >> 32));
+        uint32_t real = 0;
+        for (uint32_t t = threadIdx.x; t < tot; t += NT) {
+            const unsigned long long v = all[t];
+            if (v == ~0ull) continue;
+            ++real;
+            const uint32_t rr = t / A.k;
+            uint32_t rank = t - rr * A.k;
+            for (int o = 0; o < CL && rank < (uint32_t)A.k; ++o) {
+                if (o == (int)rr) continue;
+                const unsigned long long* lst = all + o * A.k;
+                int lo = 0, hi = A.k;  // keys < v in list o
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (lst[mid] < v) lo = mid + 1; else hi = mid;
+                }
+                rank += lo;
+            }
+            if (rank < (uint32_t)A.k) {
+                A.out_ids[b * A.k + rank] = (int32_t)(uint32_t)(v & 0xffffffffu);
+                A.out_dist[b * A.k + rank] = __uint_as_float((uint32_t)(v >> 32));
+            }
+        }
+        if (real) atomicAdd(nreal, real);
+        __syncthreads();
+        // fewer than k real keys in total: pad the tail
+        for (uint32_t t = *nreal + threadIdx.x; t < (uint32_t)A.k; t += NT) {
+            A.out_ids[b * A.k + t] = -1;
+            A.out_dist[b * A.k + t] = __int_as_float(0x7f800000);
         }
     }
     cluster_sync();  // #5: remote reads of the published top-k lists are done
@@ -716,7 +918,7 @@ struct Layout {
     size_t smem = 0;
 };
 
-int make_layout(const DeviceIndex* ix, int CL, int nsmax, uint32_t C, int k, Layout* L)
+int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, int k, Layout* L)
 {
     QArgs& A = L->A;
     memset(&A, 0, sizeof(A));
@@ -725,31 +927,34 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, uint32_t C, int k, Lay
     A.k = k;
     A.k_pad = (k + 1) & ~1;
     A.per_cta = (C + CL - 1) / CL;
+    A.span = (uint32_t)(A.cpc * ix->n_ch);
+    A.G = A.span / 32;
     const int sk = ix->sqrtK;
+    const int NC = nsmax + 2;
     uint64_t o = 0;
     A.o_tab = (uint32_t)o;
-    A.tab_stride = align16(16 + 10ull * sk);
+    A.tab_stride = align16(20 + 16ull * sk);
     o = align16(o + (uint64_t)ix->Ns * A.tab_stride);
     A.o_q = (uint32_t)o;
     o = align16(o + 4ull * ix->ld);
     A.o_hist = (uint32_t)o;
     o = align16(o + 4ull * (256 + 64));
     A.o_misc = (uint32_t)o;
-    o = align16(o + 8ull * 16 + 4ull * (32 + 16));
+    o = align16(o + 4ull * 128);
     A.o_cnt = (uint32_t)o;
-    o = align16(o + 4ull * (nsmax + 2) * (CL + 1));
+    o = align16(o + 4ull * NC * (1 + CL + NT / 32));
     A.o_seg = (uint32_t)o;
-    o = align16(o + 4ull * (2 * MAXSEG + 1));
+    o = align16(o + 4ull * (3 * MAXSEG + 1));
     A.o_slots = (uint32_t)o;
     o = align16(o + 4ull * A.per_cta);
     A.o_union = (uint32_t)o;
-    const uint64_t score_bytes = (uint64_t)A.cpc * ix->n_ch;
-    A.score_words = (uint32_t)(score_bytes / 4);
+    const uint64_t plane_bytes = 4ull * ix->Ns * A.G;
+    const uint64_t s3_bytes = 4ull * NB + 12ull * MCAP;
     const uint32_t rt = std::min<uint32_t>(RTILE, std::max<uint32_t>(A.per_cta, 1));
     A.sortP = next_pow2((uint32_t)k + rt);
-    A.mergeP = next_pow2((uint32_t)(CL * k));
+    A.mergeP = (uint32_t)(CL * k);
     const uint64_t keys_bytes = 8ull * (A.k_pad + std::max(A.sortP, A.mergeP));
-    o = align16(o + std::max(score_bytes, keys_bytes));
+    o = align16(o + std::max(plane_bytes, std::max(s3_bytes, keys_bytes)));
     L->smem = o;
     return SUCO_OK;
 }
@@ -795,19 +1000,19 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     if (CL) {
         if (CL != 1 && CL != 2 && CL != 4 && CL != 8 && CL != 16)
             return fail(SUCO_EINVAL, "cluster_size must be 0, 1, 2, 4, 8 or 16 (got %d)", CL);
-        make_layout(ix, CL, nsmax, (uint32_t)C, p->k, &L);
+        make_layout(ix, CL, nsmax, NT, (uint32_t)C, p->k, &L);
         if (L.smem > (size_t)dev_smem)
             return fail(SUCO_EUNSUPPORTED, "cluster_size %d needs %zu bytes of shared memory per CTA (max %d)", CL,
                         L.smem, dev_smem);
     } else {
         for (CL = 1; CL <= 16; CL *= 2) {
-            make_layout(ix, CL, nsmax, (uint32_t)C, p->k, &L);
+            make_layout(ix, CL, nsmax, NT, (uint32_t)C, p->k, &L);
             if (L.smem <= (size_t)dev_smem) break;
         }
         if (CL > 16)
             return fail(SUCO_EUNSUPPORTED,
-                        "n=%lld needs more than 16 CTAs of shared memory per query (SC-score array too large)",
-                        (long long)ix->n);
+                        "n=%lld with Ns=%d needs more than 16 CTAs of shared memory per query (bit planes too large)",
+                        (long long)ix->n, ix->Ns);
     }
     if (nq * CL > 0x7fffffffLL) return fail(SUCO_EINVAL, "too many queries in one call");
     QArgs& A = L.A;
