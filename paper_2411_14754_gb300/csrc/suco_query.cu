@@ -18,16 +18,20 @@
 //       that row in r2 order: the retrieved set is a "staircase", published as
 //       row prefix sums.  CTA r handles the subspaces i with i % CL == r.
 //   S4  SC-score counting (Definition 4).  Each CTA owns a contiguous id range
-//       and keeps, per subspace, one bit per id in shared memory ("collided in
-//       subspace i").  It lists its part of every retrieved cell's id list (the
-//       index's chunk splits), load-balances the flattened list over warps and
-//       sets the bits with shared-memory atomicOr.
-//   S5  candidate selection.  Bit-sliced adders turn the Ns bit planes of 32
-//       ids into their SC-scores; per-warp counts of scores >= s are summed over
-//       the cluster through distributed shared memory; theta is the largest s
-//       with at least C scores >= s; every id above theta and the lowest-id ties
-//       at theta (C in total) are written, in id order, straight into the
-//       candidate slots of the CTA that re-ranks them.
+//       and keeps its SC-scores bit-sliced in shared memory: B = bits(Ns) planes
+//       of one bit per id.  It lists its part of every retrieved cell's id list
+//       of every subspace (the index's chunk splits), load-balances the
+//       flattened list over warps and adds 1 to each listed id's count with a
+//       ripple of shared-memory atomicXor: level j is toggled, and the carry
+//       moves to level j+1 while the returned old bit was 1.  For m toggles of a
+//       bit that starts at 0, exactly floor(m/2) return 1 whatever their order,
+//       so concurrent increments of the same id still count exactly.
+//   S5  candidate selection.  Per-warp counts of scores >= s (bitwise
+//       comparisons of the sliced counts) are summed over the cluster through
+//       distributed shared memory; theta is the largest s with at least C
+//       scores >= s; every id above theta and the lowest-id ties at theta
+//       (C in total) are written, in id order, straight into the candidate
+//       slots of the CTA that re-ranks them.
 //   S6  exact re-rank: every CTA computes FP32 squared distances of its share
 //       of the C candidates (one warp per row, several rows in flight per warp),
 //       keeps a local top-k by (distance, id), and CTA 0 merges the CL sorted
@@ -40,11 +44,13 @@
 namespace suco {
 namespace {
 
-constexpr int MAXSEG = 2048;  // retrieved-cell segments listed per scan round
-constexpr int RTILE = 2048;   // candidates per re-rank round
+constexpr int MAXSEG = 1024;  // retrieved-cell segments listed per scan round
 constexpr int NB = 1024;      // linear value buckets of the cut search
 constexpr int MCAP = 1024;    // cells of the crossing bucket resolved from a list
 constexpr int SCAN_U = 8;     // ids in flight per lane in the scan
+
+constexpr int S3_BYTES = 4 * NB + 12 * MCAP;  // S3 scratch at the start of the union region
+constexpr int SURV_CAP = 512; // keys kept for the final sort of a local top-k
 
 struct QArgs {
     const float* __restrict__ X;
@@ -63,6 +69,7 @@ struct QArgs {
     int32_t k, k_pad;
     uint32_t T, C, per_cta;
     uint32_t span, G;  // ids per CTA, 32-id groups per CTA
+    uint32_t nbits;    // B: bit planes of the sliced SC-score counts
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -71,8 +78,10 @@ struct QArgs {
     uint8_t* dbg_scores;
     int32_t* dbg_cands;
     // shared-memory layout (byte offsets)
-    uint32_t o_tab, tab_stride, o_q, o_hist, o_misc, o_cnt, o_seg, o_slots, o_union;
-    uint32_t sortP, mergeP;
+    uint32_t o_tab, tab_stride, o_q, o_hist, o_misc, o_cnt, o_seg, o_slots, o_keys, o_union;
+    uint32_t sortP;       // power of two >= the CTA's candidate share (fallback sort)
+    uint32_t stage_cent;  // 1: the subspace's centroids are staged in shared memory
+    uint32_t rows_half;   // candidate rows per half of the S6 double buffer
 };
 
 // ---------------------------------------------------------------------------
@@ -112,6 +121,22 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr)
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v)
 {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy (cached in L2 only), and its groups
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)),
+                 "l"(__cvta_generic_to_global(gsrc))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -223,17 +248,37 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
     const int soff = i * A.sub_s;
     const int slen = (i == A.Ns - 1) ? A.d - (A.Ns - 1) * A.sub_s : A.sub_s;
     const int first = slen / 2;
-    // S1: squared distances to the 2*sqrtK half-subspace centroids
+    // S1: squared distances to the 2*sqrtK half-subspace centroids.  The
+    // subspace's centroids are staged dimension-major ([h][j][a]) so that
+    // consecutive threads read consecutive words.
+    const float* cg = A.cent + (int64_t)i * 2 * sk * A.hmax;
+    float* cst = reinterpret_cast<float*>(smem + A.o_union + S3_BYTES);
+    if (A.stage_cent) {
+        for (int t = threadIdx.x; t < 2 * sk * A.hmax; t += NT) {
+            const int j = t % A.hmax, ha = t / A.hmax;
+            const int h = ha >= sk, a = ha - h * sk;
+            cst[(h * A.hmax + j) * sk + a] = __ldg(cg + t);
+        }
+        __syncthreads();
+    }
     for (int t = threadIdx.x; t < 2 * sk; t += NT) {
         const int h = t >= sk;
         const int a = t - h * sk;
         const int off = soff + (h ? first : 0);
         const int len = h ? slen - first : first;
-        const float* c = A.cent + ((int64_t)(i * 2 + h) * sk + a) * A.hmax;
         float acc = 0.f;
-        for (int j = 0; j < len; ++j) {
-            const float df = __fsub_rn(qs[off + j], __ldg(c + j));
-            acc = __fmaf_rn(df, df, acc);
+        if (A.stage_cent) {
+            const float* c = cst + h * A.hmax * sk + a;
+            for (int j = 0; j < len; ++j) {
+                const float df = __fsub_rn(qs[off + j], c[j * sk]);
+                acc = __fmaf_rn(df, df, acc);
+            }
+        } else {
+            const float* c = cg + (int64_t)(h * sk + a) * A.hmax;
+            for (int j = 0; j < len; ++j) {
+                const float df = __fsub_rn(qs[off + j], __ldg(c + j));
+                acc = __fmaf_rn(df, df, acc);
+            }
         }
         (h ? tb.d2 : tb.d1)[a] = acc;
     }
@@ -261,7 +306,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
     uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
     uint32_t* h256 = reinterpret_cast<uint32_t*>(smem + A.o_hist);
     unsigned long long* bc = reinterpret_cast<unsigned long long*>(smem + A.o_misc);
-    uint32_t* mcount = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 10;
+    uint32_t* mcount = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 14;
     const uint32_t* co = A.cell_off + (int64_t)i * (A.K + 1);
     const float smin = __fadd_rn(tb.d1[tb.idx1[0]], tb.d2[tb.idx2[0]]);
     const float smax = __fadd_rn(tb.d1[tb.idx1[sk - 1]], tb.d2[tb.idx2[sk - 1]]);
@@ -331,9 +376,76 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
     __syncthreads();
     const uint32_t nm = *mcount;
     const bool listed = nm <= MCAP;
-    // weighted radix select of the cut key over the bucket's members
     unsigned long long prefix = 0, mask = 0, last_w = 0;
-    for (int pass = 0; pass < 6; ++pass) {
+    int pass0 = 0;
+    if (nm <= 32) {
+        // few members: one warp sorts them by key and walks the weight prefix
+        if (threadIdx.x < 32) {
+            unsigned long long key = lane < (int)nm ? mkey[lane] : ~0ull;
+            uint32_t w = lane < (int)nm ? mw[lane] : 0u;
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, stride);
+                    const uint32_t ow = __shfl_xor_sync(0xffffffffu, w, stride);
+                    const bool lower = (lane & stride) == 0;
+                    const bool asc = (lane & size) == 0;
+                    const bool take_other = lower == asc ? ok < key : ok > key;
+                    if (take_other) {
+                        key = ok;
+                        w = ow;
+                    }
+                }
+            }
+            uint32_t incl = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t need = (uint32_t)(A.T - below);
+            const uint32_t hit = __ballot_sync(0xffffffffu, incl >= need && lane < (int)nm);
+            const int src = __ffs(hit) - 1;
+            const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
+            const uint32_t ii = __shfl_sync(0xffffffffu, incl, src);
+            if (lane == 0) {
+                bc[0] = kk;
+                bc[1] = ii;
+            }
+        }
+        __syncthreads();
+        prefix = bc[0];
+        last_w = 0;
+        below += bc[1];
+        pass0 = 6;
+        __syncthreads();
+    } else if (listed) {
+        // bytes shared by every member are already decided
+        unsigned long long* kmm = bc + 5;  // [5] = min, [6] = max
+        if (threadIdx.x == 0) {
+            kmm[0] = ~0ull;
+            kmm[1] = 0ull;
+        }
+        __syncthreads();
+        unsigned long long lo = ~0ull, hi = 0ull;
+        for (uint32_t m = threadIdx.x; m < nm; m += NT) {
+            lo = min(lo, mkey[m]);
+            hi = max(hi, mkey[m]);
+        }
+        if (lo != ~0ull) atomicMin(&kmm[0], lo);
+        if (hi) atomicMax(&kmm[1], hi);
+        __syncthreads();
+        const unsigned long long diff = kmm[0] ^ kmm[1];
+        while (pass0 < 6 && ((diff >> (40 - 8 * pass0)) & 255ull) == 0) {
+            mask |= 255ull << (40 - 8 * pass0);
+            ++pass0;
+        }
+        prefix = kmm[0] & mask;
+        __syncthreads();
+    }
+    // weighted radix select of the cut key over the bucket's members
+    for (int pass = pass0; pass < 6; ++pass) {
         const int shift = 40 - 8 * pass;
         for (int t = threadIdx.x; t < 256; t += NT) h256[t] = 0u;
         __syncthreads();
@@ -398,6 +510,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
         last_w = bc[2];
         __syncthreads();
     }
+    // after the warp path `below` already counts the cut cell itself
     // the staircase: retrieved cells of ranked row rho are its first columns in
     // r2 order (the key grows along the row); store lengths, then prefix sums
     for (int rho = threadIdx.x; rho < sk; rho += NT) {
@@ -454,16 +567,16 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
     __syncthreads();
 }
 
-// S4 for the retrieved-cell list entries [e0, e0+m): build the segments, then
-// set the collision bits of their ids.
-template <int NT>
+// S4 for entries [e0, e0+m) of the flattened retrieved-cell list (all
+// subspaces, subspace-major): build the segments (this CTA's part of each
+// cell's id list), then increment the sliced counts of their ids.
+template <int NT, int B>
 __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t m, const uint32_t* sub_pre,
-                              uint32_t id0, int j0, int j1)
+                              uint32_t* planes, uint32_t id0, int j0, int j1)
 {
-    uint32_t* planes = reinterpret_cast<uint32_t*>(smem + A.o_union);
-    uint32_t* seg_start = reinterpret_cast<uint32_t*>(smem + A.o_seg);
-    uint32_t* seg_plane = seg_start + MAXSEG;
-    uint32_t* seg_pre = seg_plane + MAXSEG;  // [MAXSEG+1]
+    // per segment: perm index of its first id minus its flat start
+    uint32_t* seg_base = reinterpret_cast<uint32_t*>(smem + A.o_seg);
+    uint32_t* seg_pre = seg_base + MAXSEG;  // [MAXSEG+1]
     uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
     const int sk = A.sqrtK;
     constexpr int EPT = MAXSEG / NT;
@@ -489,8 +602,7 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
             const uint32_t s0 = __ldg(sp + (int64_t)j0 * A.K);
             const uint32_t s1 = __ldg(sp + (int64_t)j1 * A.K);
             len[u] = s1 - s0;
-            seg_start[e] = (uint32_t)i * (uint32_t)A.n + s0;
-            seg_plane[e] = (uint32_t)i * A.G;
+            seg_base[e] = (uint32_t)i * (uint32_t)A.n + s0;
         }
         s += len[u];
     }
@@ -499,7 +611,10 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
         const uint32_t e = threadIdx.x * EPT + u;
-        if (e < m) seg_pre[e] = run;
+        if (e < m) {
+            seg_pre[e] = run;
+            seg_base[e] -= run;  // perm index = base + flat position (mod 2^32)
+        }
         run += len[u];
     }
     if (threadIdx.x == 0) seg_pre[m] = F;
@@ -520,51 +635,41 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
         const uint32_t span = A.span;
         for (; p < we; p += 32 * SCAN_U) {
             int32_t idv[SCAN_U];
-            uint32_t pl[SCAN_U];
 #pragma unroll
             for (int u = 0; u < SCAN_U; ++u) {
                 const uint32_t pu = p + 32 * u;
                 idv[u] = -1;
-                pl[u] = 0;
                 if (pu < we) {
                     while (seg_pre[sg + 1] <= pu) ++sg;
-                    idv[u] = __ldg(A.perm + seg_start[sg] + (pu - seg_pre[sg]));
-                    pl[u] = seg_plane[sg];
+                    idv[u] = __ldg(A.perm + (uint32_t)(seg_base[sg] + pu));
                 }
             }
+            uint32_t word[SCAN_U], carry[SCAN_U];
 #pragma unroll
-            for (int u = 0; u < SCAN_U; ++u)
-                if (idv[u] >= 0) {
-                    const uint32_t loc = (uint32_t)idv[u] - id0;
-                    if (loc < span) atomicOr(&planes[pl[u] + (loc >> 5)], 1u << (loc & 31u));
-                }
+            for (int u = 0; u < SCAN_U; ++u) {
+                const uint32_t loc = (uint32_t)idv[u] - id0;
+                const bool ok = idv[u] >= 0 && loc < span;
+                word[u] = ok ? loc >> 5 : 0u;
+                carry[u] = ok ? 1u << (loc & 31u) : 0u;
+            }
+            // add 1: toggle level j; carry on while the old bit was set
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+#pragma unroll
+                for (int u = 0; u < SCAN_U; ++u)
+                    if (carry[u]) carry[u] &= atomicXor(&planes[(uint32_t)j * A.G + word[u]], carry[u]);
+            }
         }
     }
     __syncthreads();
 }
 
-// Bit-sliced SC-scores of 32 ids: acc[j] holds bit j of every id's count.
-template <int NSMAX, int B>
-__device__ __forceinline__ void bitsliced_scores(const uint32_t* planes, uint32_t G, int Ns, uint32_t g,
-                                                 uint32_t acc[B])
+// The sliced SC-scores of 32-id group g: acc[j] holds bit j of each id's score.
+template <int B>
+__device__ __forceinline__ void load_scores(const uint32_t* planes, uint32_t G, uint32_t g, uint32_t acc[B])
 {
 #pragma unroll
-    for (int j = 0; j < B; ++j) acc[j] = 0u;
-#pragma unroll
-    for (int i = 0; i < NSMAX; ++i) {
-        if (i < Ns) {
-            uint32_t carry = planes[(uint32_t)i * G + g];
-            // after i+1 planes a count needs at most bits(i+1) bits
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-                if ((1 << j) <= i + 1) {
-                    const uint32_t t = acc[j] & carry;
-                    acc[j] ^= carry;
-                    carry = t;
-                }
-            }
-        }
-    }
+    for (int j = 0; j < B; ++j) acc[j] = planes[(uint32_t)j * G + g];
 }
 
 // Bitwise "score >= s" over the 32 ids of a bit-sliced accumulator.
@@ -579,7 +684,7 @@ __device__ __forceinline__ uint32_t bitsliced_ge(const uint32_t acc[B], uint32_t
 }
 
 template <int NT, int NSMAX>
-__global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
+__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const QArgs A)
 {
     extern __shared__ __align__(16) char smem[];
     constexpr int B = NSMAX == 8 ? 4 : (NSMAX == 16 ? 5 : 6);
@@ -608,7 +713,7 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
     {
         uint4* pw = reinterpret_cast<uint4*>(smem + A.o_union);
         const uint4 z = make_uint4(0, 0, 0, 0);
-        const uint32_t n16 = ((uint32_t)A.Ns * A.G + 3) / 4;  // the union region is a multiple of 16 bytes
+        const uint32_t n16 = (B * A.G + 3) / 4;  // the union region is a multiple of 16 bytes
         for (uint32_t w = threadIdx.x; w < n16; w += NT) pw[w] = z;
     }
     cluster_sync();  // #1: every subspace's cut and staircase are published
@@ -639,16 +744,16 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
         sub_pre[A.Ns] = acc;
     }
     __syncthreads();
+    uint32_t* planes = reinterpret_cast<uint32_t*>(smem + A.o_union);  // [B][G] sliced counts
     const uint32_t L = sub_pre[A.Ns];
     for (uint32_t e0 = 0; e0 < L; e0 += MAXSEG)
-        scan_segments<NT>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, id0, j0, j1);
+        scan_segments<NT, B>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, planes, id0, j0, j1);
 
-    const uint32_t* planes = reinterpret_cast<const uint32_t*>(smem + A.o_union);
     const uint32_t valid = id0 >= A.n ? 0u : (uint32_t)min((int64_t)A.span, A.n - (int64_t)id0);
     if (A.dbg_scores)
         for (uint32_t j = threadIdx.x; j < valid; j += NT) {
             uint32_t sc = 0;
-            for (int i = 0; i < A.Ns; ++i) sc += (planes[(uint32_t)i * A.G + (j >> 5)] >> (j & 31)) & 1u;
+            for (int q = 0; q < B; ++q) sc |= ((planes[(uint32_t)q * A.G + (j >> 5)] >> (j & 31)) & 1u) << q;
             A.dbg_scores[b * A.n + id0 + j] = (uint8_t)sc;
         }
 
@@ -665,7 +770,7 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
         for (int s = 0; s < NSMAX; ++s) c[s] = 0u;
         for (uint32_t g = gb + lane; g < ge; g += 32) {
             uint32_t acc[B];
-            bitsliced_scores<NSMAX, B>(planes, A.G, A.Ns, g, acc);
+            load_scores<B>(planes, A.G, g, acc);
 #pragma unroll
             for (int s = 0; s < NSMAX; ++s)
                 if (s < A.Ns) c[s] += __popc(bitsliced_ge<B>(acc, (uint32_t)(s + 1)));
@@ -742,7 +847,7 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
             uint32_t gm = 0, em = 0;
             if (g < ge) {
                 uint32_t acc[B];
-                bitsliced_scores<NSMAX, B>(planes, A.G, A.Ns, g, acc);
+                load_scores<B>(planes, A.G, g, acc);
                 gm = bitsliced_ge<B>(acc, theta + 1);
                 em = bitsliced_ge<B>(acc, theta) & ~gm;
                 const uint32_t base = g * 32;
@@ -792,83 +897,200 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
     cluster_sync();  // #3: every candidate slot is filled; the bit planes are dead
 
     // ---- S6: exact FP32 re-rank of this CTA's share of the candidates
-    unsigned long long* topk = reinterpret_cast<unsigned long long*>(smem + A.o_union);
-    unsigned long long* sortbuf = topk + A.k_pad;
     const uint32_t* slots = reinterpret_cast<const uint32_t*>(smem + A.o_slots);
     const uint32_t mine = A.C > r * A.per_cta ? min(A.per_cta, A.C - r * A.per_cta) : 0u;
-    const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + A.o_keys);  // [sortP]
     const int ld4 = (int)(A.ld / 4);
-    constexpr int RW = NT == 1024 ? 4 : 8;  // rows in flight per warp (register budget)
-    uint32_t kc = 0;
-    for (uint32_t t0 = 0; t0 < mine; t0 += RTILE) {
-        const uint32_t tc = min((uint32_t)RTILE, mine - t0);
-        for (uint32_t t = threadIdx.x; t < (uint32_t)A.sortP; t += NT)
-            if (t < kc) sortbuf[t] = topk[t]; else if (t >= kc + tc) sortbuf[t] = ~0ull;
-        for (uint32_t j = (uint32_t)warp * RW; j < tc; j += NW * RW) {
-            int32_t id[RW];
-            float acc[RW];
-#pragma unroll
-            for (int u = 0; u < RW; ++u) {
-                const uint32_t sv = j + u < tc ? slots[t0 + j + u] : 0xffffffffu;
-                id[u] = sv < (uint32_t)A.n ? (int32_t)sv : -1;
-                acc[u] = 0.f;
-            }
+    const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
+    float4* rowbuf = reinterpret_cast<float4*>(smem + A.o_union);  // two halves of rows_half rows
+    const uint32_t RH = A.rows_half;
+    // rows [r0, r0+RH) of the share go into half h with 16-byte asynchronous copies
+    auto issue = [&](uint32_t r0, uint32_t h) {
+        const uint32_t nr = min(RH, mine - r0);
+        float4* dst = rowbuf + (size_t)h * RH * ld4;
+        for (uint32_t rr = (uint32_t)warp; rr < nr; rr += NW) {
+            const uint32_t id = slots[r0 + rr];
+            if (id >= (uint32_t)A.n) continue;
+            const float4* src = reinterpret_cast<const float4*>(A.X + (int64_t)id * A.ld);
+            for (int c = lane; c < ld4; c += 32) cp_async16(dst + (size_t)rr * ld4 + c, src + c);
+        }
+        cp_async_commit();
+    };
+    if (mine > 0) issue(0, 0);
+    uint32_t half = 0;
+    for (uint32_t r0 = 0; r0 < mine; r0 += RH, half ^= 1u) {
+        if (r0 + RH < mine) {
+            issue(r0 + RH, half ^ 1u);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const uint32_t nr = min(RH, mine - r0);
+        const float4* src = rowbuf + (size_t)half * RH * ld4;
+        for (uint32_t rr = (uint32_t)warp; rr < nr; rr += NW) {
+            const uint32_t id = slots[r0 + rr];
+            float acc = 0.f;
             for (int c = lane; c < ld4; c += 32) {
+                const float4 xv = src[(size_t)rr * ld4 + c];
                 const float4 qv = q4[c];
-                float4 xv[RW];
-#pragma unroll
-                for (int u = 0; u < RW; ++u)
-                    if (id[u] >= 0) xv[u] = __ldg(reinterpret_cast<const float4*>(A.X + (int64_t)id[u] * A.ld) + c);
-#pragma unroll
-                for (int u = 0; u < RW; ++u)
-                    if (id[u] >= 0) {
-                        float df = __fsub_rn(xv[u].x, qv.x);
-                        acc[u] = __fmaf_rn(df, df, acc[u]);
-                        df = __fsub_rn(xv[u].y, qv.y);
-                        acc[u] = __fmaf_rn(df, df, acc[u]);
-                        df = __fsub_rn(xv[u].z, qv.z);
-                        acc[u] = __fmaf_rn(df, df, acc[u]);
-                        df = __fsub_rn(xv[u].w, qv.w);
-                        acc[u] = __fmaf_rn(df, df, acc[u]);
-                    }
+                float df = __fsub_rn(xv.x, qv.x);
+                acc = __fmaf_rn(df, df, acc);
+                df = __fsub_rn(xv.y, qv.y);
+                acc = __fmaf_rn(df, df, acc);
+                df = __fsub_rn(xv.z, qv.z);
+                acc = __fmaf_rn(df, df, acc);
+                df = __fsub_rn(xv.w, qv.w);
+                acc = __fmaf_rn(df, df, acc);
             }
 #pragma unroll
-            for (int u = 0; u < RW; ++u) {
-                float v = acc[u];
+            for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+            if (lane == 0)
+                keys[r0 + rr] = id < (uint32_t)A.n ? ((unsigned long long)__float_as_uint(acc) << 32) | id : ~0ull;
+        }
+        __syncthreads();  // this half may be refilled two rounds later
+    }
+
+    // local top-k: a linear bucket histogram of the distances finds a bucket
+    // that holds the k-th smallest; only keys up to it are sorted
+    uint32_t* khist = reinterpret_cast<uint32_t*>(smem + A.o_union);               // [NB]
+    unsigned long long* surv = reinterpret_cast<unsigned long long*>(khist + NB);   // [SURV_CAP]
+    uint32_t* kv = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 100;             // min, max, bucket, count
+    const uint32_t k = (uint32_t)A.k;
+    unsigned long long* best = keys;  // sorted top-k ends up here
+    uint32_t nbest = 0;
+    if (mine <= 2 * k || mine <= 64) {
+        for (uint32_t t = mine + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
+        __syncthreads();
+        block_bitonic_sort<NT>(keys, (int)A.sortP);
+        nbest = min(k, mine);
+    } else {
+        if (threadIdx.x == 0) {
+            kv[0] = 0xffffffffu;
+            kv[1] = 0u;
+            kv[3] = 0u;
+        }
+        for (int t = threadIdx.x; t < NB; t += NT) khist[t] = 0u;
+        __syncthreads();
+        uint32_t lo = 0xffffffffu, hi = 0u;
+        for (uint32_t t = threadIdx.x; t < mine; t += NT) {
+            const unsigned long long v = keys[t];
+            if (v == ~0ull) continue;
+            const uint32_t db = (uint32_t)(v >> 32);
+            lo = min(lo, db);
+            hi = max(hi, db);
+        }
+        if (lo != 0xffffffffu) atomicMin(&kv[0], lo);
+        if (hi) atomicMax(&kv[1], hi);
+        __syncthreads();
+        const float dmin = __uint_as_float(kv[0]);
+        const float drange = __fsub_rn(__uint_as_float(kv[1]), dmin);
+        const float dscale = drange > 0.f ? __fdiv_rn((float)NB, drange) : 0.f;
+        for (uint32_t t = threadIdx.x; t < mine; t += NT) {
+            const unsigned long long v = keys[t];
+            if (v != ~0ull) atomicAdd(&khist[value_bucket(__uint_as_float((uint32_t)(v >> 32)), dmin, dscale)], 1u);
+        }
+        __syncthreads();
+        {
+            constexpr int BPT = NB / NT > 0 ? NB / NT : 1;
+            uint32_t v[BPT], sum = 0;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
-                if (lane == 0 && j + u < tc)
-                    sortbuf[kc + j + u] =
-                        id[u] >= 0 ? ((unsigned long long)__float_as_uint(v) << 32) | (uint32_t)id[u] : ~0ull;
+            for (int u = 0; u < BPT; ++u) {
+                const int e = threadIdx.x * BPT + u;
+                v[u] = e < NB ? khist[e] : 0u;
+                sum += v[u];
+            }
+            uint32_t tot;
+            uint32_t run = block_exclusive_scan<NT>(sum, reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256, &tot);
+#pragma unroll
+            for (int u = 0; u < BPT; ++u) {
+                const int e = threadIdx.x * BPT + u;
+                if (e < NB && ((run < k && run + v[u] >= k) || (tot < k && e == NB - 1))) {
+                    kv[2] = (uint32_t)e;
+                    kv[3] = run + v[u];
+                }
+                run += v[u];
             }
         }
         __syncthreads();
-        block_bitonic_sort<NT>(sortbuf, (int)A.sortP);
-        kc = min((uint32_t)A.k, kc + tc);
-        for (uint32_t t = threadIdx.x; t < kc; t += NT) topk[t] = sortbuf[t];
-        __syncthreads();
+        const uint32_t kb = kv[2], ns = kv[3];
+        if (ns <= SURV_CAP) {
+            uint32_t* ctr = kv + 4;
+            if (threadIdx.x == 0) *ctr = 0u;
+            __syncthreads();
+            for (uint32_t t = threadIdx.x; t < mine; t += NT) {
+                const unsigned long long v = keys[t];
+                if (v != ~0ull && (uint32_t)value_bucket(__uint_as_float((uint32_t)(v >> 32)), dmin, dscale) <= kb)
+                    surv[atomicAdd(ctr, 1u)] = v;
+            }
+            __syncthreads();
+            if (ns <= 64) {
+                // one warp sorts up to 64 keys in registers (bitonic network over
+                // element e = slot*32 + lane; stride 32 pairs the two slots of a lane)
+                if (warp == 0) {
+                    unsigned long long v[2];
+                    v[0] = (uint32_t)lane < ns ? surv[lane] : ~0ull;
+                    v[1] = (uint32_t)lane + 32 < ns ? surv[lane + 32] : ~0ull;
+#pragma unroll
+                    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+                        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                            if (stride == 32) {
+                                if (v[0] > v[1]) {  // size 64: ascending, slot 0 is the lower element
+                                    const unsigned long long t = v[0];
+                                    v[0] = v[1];
+                                    v[1] = t;
+                                }
+                            } else {
+#pragma unroll
+                                for (int sl = 0; sl < 2; ++sl) {
+                                    const int e = sl * 32 + lane;
+                                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[sl], stride);
+                                    const bool lower = (e & stride) == 0, asc = (e & size) == 0;
+                                    if (lower == asc ? o < v[sl] : o > v[sl]) v[sl] = o;
+                                }
+                            }
+                        }
+                    }
+                    surv[lane] = v[0];
+                    surv[lane + 32] = v[1];
+                }
+                __syncthreads();
+            } else {
+                uint32_t P = 1;
+                while (P < ns) P <<= 1;
+                for (uint32_t t = ns + threadIdx.x; t < P; t += NT) surv[t] = ~0ull;
+                __syncthreads();
+                block_bitonic_sort<NT>(surv, (int)P);
+            }
+            best = surv;
+            nbest = min(k, ns);
+        } else {
+            // a crowded bucket (many equal distances): sort the whole share
+            for (uint32_t t = mine + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
+            __syncthreads();
+            block_bitonic_sort<NT>(keys, (int)A.sortP);
+            nbest = min(k, mine);
+        }
     }
-    for (uint32_t t = kc + threadIdx.x; t < (uint32_t)A.k; t += NT) topk[t] = ~0ull;
-    cluster_sync();  // #4: every local top-k is published (sorted, padded to k)
+    // hand the sorted local list (padded to k) to CTA 0
+    {
+        unsigned long long* recv = reinterpret_cast<unsigned long long*>(smem + A.o_seg);  // [CL][k] on CTA 0
+        const uint32_t rb = map_rank(smem_addr(recv + (size_t)r * k), 0u);
+        for (uint32_t t = threadIdx.x; t < k; t += NT) {
+            const unsigned long long v = t < nbest ? best[t] : ~0ull;
+            st_cluster_u32(rb + 8u * t, (uint32_t)v);
+            st_cluster_u32(rb + 8u * t + 4u, (uint32_t)(v >> 32));
+        }
+    }
+    cluster_sync();  // #4: every local top-k is in CTA 0; the other CTAs are done
 
     if (r == 0) {
         // merge by rank: a key's final position is the number of smaller keys
         // over all CL sorted lists (keys are unique because ids are)
-        const uint32_t tot = (uint32_t)CL * A.k;
-        unsigned long long* all = sortbuf;
-        for (uint32_t t = threadIdx.x; t < tot; t += NT) {
-            const uint32_t rr = t / A.k, e = t - rr * A.k;
-            unsigned long long v;
-            if (rr == 0) {
-                v = topk[e];
-            } else {
-                const uint32_t ad = map_rank(smem_addr(topk + e), rr);
-                const uint32_t lo = ld_cluster_u32(ad), hi = ld_cluster_u32(ad + 4);
-                v = ((unsigned long long)hi << 32) | lo;
-            }
-            all[t] = v;
-        }
-        uint32_t* nreal = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 96;
+        const unsigned long long* all = reinterpret_cast<const unsigned long long*>(smem + A.o_seg);
+        const uint32_t tot = (uint32_t)CL * k;
+        uint32_t* nreal = kv + 5;
         if (threadIdx.x == 0) *nreal = 0u;
         __syncthreads();
         uint32_t real = 0;
@@ -876,32 +1098,31 @@ __global__ void __launch_bounds__(NT, 1) suco_query_kernel(const QArgs A)
             const unsigned long long v = all[t];
             if (v == ~0ull) continue;
             ++real;
-            const uint32_t rr = t / A.k;
-            uint32_t rank = t - rr * A.k;
-            for (int o = 0; o < CL && rank < (uint32_t)A.k; ++o) {
+            const uint32_t rr = t / k;
+            uint32_t rank = t - rr * k;
+            for (int o = 0; o < CL && rank < k; ++o) {
                 if (o == (int)rr) continue;
-                const unsigned long long* lst = all + o * A.k;
-                int lo = 0, hi = A.k;  // keys < v in list o
+                const unsigned long long* lst = all + (size_t)o * k;
+                uint32_t lo = 0, hi = k;  // keys < v in list o
                 while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
+                    const uint32_t mid = (lo + hi) >> 1;
                     if (lst[mid] < v) lo = mid + 1; else hi = mid;
                 }
                 rank += lo;
             }
-            if (rank < (uint32_t)A.k) {
-                A.out_ids[b * A.k + rank] = (int32_t)(uint32_t)(v & 0xffffffffu);
-                A.out_dist[b * A.k + rank] = __uint_as_float((uint32_t)(v >> 32));
+            if (rank < k) {
+                A.out_ids[b * k + rank] = (int32_t)(uint32_t)(v & 0xffffffffu);
+                A.out_dist[b * k + rank] = __uint_as_float((uint32_t)(v >> 32));
             }
         }
         if (real) atomicAdd(nreal, real);
         __syncthreads();
         // fewer than k real keys in total: pad the tail
-        for (uint32_t t = *nreal + threadIdx.x; t < (uint32_t)A.k; t += NT) {
-            A.out_ids[b * A.k + t] = -1;
-            A.out_dist[b * A.k + t] = __int_as_float(0x7f800000);
+        for (uint32_t t = *nreal + threadIdx.x; t < k; t += NT) {
+            A.out_ids[b * k + t] = -1;
+            A.out_dist[b * k + t] = __int_as_float(0x7f800000);
         }
     }
-    cluster_sync();  // #5: remote reads of the published top-k lists are done
 }
 
 uint32_t align16(uint64_t x) { return (uint32_t)((x + 15) & ~uint64_t(15)); }
@@ -943,18 +1164,24 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, in
     o = align16(o + 4ull * 128);
     A.o_cnt = (uint32_t)o;
     o = align16(o + 4ull * NC * (1 + CL + NT / 32));
-    A.o_seg = (uint32_t)o;
-    o = align16(o + 4ull * (3 * MAXSEG + 1));
+    A.o_seg = (uint32_t)o;  // S4 segment list; later CTA 0's inbox of the CL local top-k lists
+    o = align16(o + std::max<uint64_t>(4ull * (2 * MAXSEG + 1), 8ull * CL * k));
     A.o_slots = (uint32_t)o;
     o = align16(o + 4ull * A.per_cta);
+    A.sortP = next_pow2(std::max<uint32_t>(A.per_cta, 1));
+    A.o_keys = (uint32_t)o;
+    o = align16(o + 8ull * A.sortP);
     A.o_union = (uint32_t)o;
-    const uint64_t plane_bytes = 4ull * ix->Ns * A.G;
-    const uint64_t s3_bytes = 4ull * NB + 12ull * MCAP;
-    const uint32_t rt = std::min<uint32_t>(RTILE, std::max<uint32_t>(A.per_cta, 1));
-    A.sortP = next_pow2((uint32_t)k + rt);
-    A.mergeP = (uint32_t)(CL * k);
-    const uint64_t keys_bytes = 8ull * (A.k_pad + std::max(A.sortP, A.mergeP));
-    o = align16(o + std::max(plane_bytes, std::max(s3_bytes, keys_bytes)));
+    A.nbits = nsmax == 8 ? 4 : (nsmax == 16 ? 5 : 6);
+    const uint64_t plane_bytes = 4ull * A.nbits * A.G;
+    const uint64_t cent_bytes = 8ull * sk * ix->hmax;
+    A.stage_cent = cent_bytes <= 65536 ? 1u : 0u;
+    const uint64_t s3_bytes = S3_BYTES + (A.stage_cent ? cent_bytes : 0);
+    const uint64_t row_bytes = 4ull * ix->ld;
+    const uint64_t s6_bytes = std::max<uint64_t>(4ull * NB + 8ull * SURV_CAP, 2 * 8 * row_bytes);
+    const uint64_t ubytes = std::max(plane_bytes, std::max(s3_bytes, s6_bytes));
+    A.rows_half = (uint32_t)std::max<uint64_t>(1, ubytes / 2 / row_bytes);
+    o = align16(o + ubytes);
     L->smem = o;
     return SUCO_OK;
 }
@@ -991,29 +1218,42 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     int64_t T = 0, C = 0;
     thresholds(ix->n, p->alpha, p->beta, p->k, &T, &C);
     const int nsmax = ix->Ns <= 8 ? 8 : (ix->Ns <= 16 ? 16 : 32);
-    const int NT = p->threads ? p->threads : 1024;
-    if (NT != 512 && NT != 1024) return fail(SUCO_EINVAL, "threads must be 0, 512 or 1024 (got %d)", p->threads);
-    int dev_smem = 0;
-    SUCO_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
-    Layout L;
+    int NT = p->threads;
+    if (NT != 0 && NT != 512 && NT != 1024) return fail(SUCO_EINVAL, "threads must be 0, 512 or 1024 (got %d)", NT);
     int CL = p->cluster_size;
-    if (CL) {
-        if (CL != 1 && CL != 2 && CL != 4 && CL != 8 && CL != 16)
-            return fail(SUCO_EINVAL, "cluster_size must be 0, 1, 2, 4, 8 or 16 (got %d)", CL);
-        make_layout(ix, CL, nsmax, NT, (uint32_t)C, p->k, &L);
-        if (L.smem > (size_t)dev_smem)
-            return fail(SUCO_EUNSUPPORTED, "cluster_size %d needs %zu bytes of shared memory per CTA (max %d)", CL,
-                        L.smem, dev_smem);
-    } else {
-        for (CL = 1; CL <= 16; CL *= 2) {
-            make_layout(ix, CL, nsmax, NT, (uint32_t)C, p->k, &L);
-            if (L.smem <= (size_t)dev_smem) break;
+    if (CL != 0 && CL != 1 && CL != 2 && CL != 4 && CL != 8 && CL != 16)
+        return fail(SUCO_EINVAL, "cluster_size must be 0, 1, 2, 4, 8 or 16 (got %d)", CL);
+    int dev_smem = 0, sm_smem = 0, reserved = 0;
+    SUCO_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
+    SUCO_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ix->device));
+    SUCO_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ix->device));
+    // two 512-thread CTAs per SM let the phases of two queries overlap
+    const size_t two_per_sm = (size_t)sm_smem / 2 - (size_t)reserved;
+    Layout L;
+    bool chosen = false;
+    for (int cl = CL ? CL : 1; cl <= (CL ? CL : 16) && !chosen; cl *= 2) {
+        if (NT == 0 || NT == 512) {
+            make_layout(ix, cl, nsmax, 512, (uint32_t)C, p->k, &L);
+            if (L.smem <= two_per_sm || (NT == 512 && L.smem <= (size_t)dev_smem)) {
+                CL = cl;
+                NT = 512;
+                chosen = true;
+            }
         }
-        if (CL > 16)
-            return fail(SUCO_EUNSUPPORTED,
-                        "n=%lld with Ns=%d needs more than 16 CTAs of shared memory per query (bit planes too large)",
-                        (long long)ix->n, ix->Ns);
     }
+    for (int cl = CL ? CL : 1; cl <= (CL ? CL : 16) && !chosen; cl *= 2) {
+        const int nt = NT ? NT : 1024;
+        make_layout(ix, cl, nsmax, nt, (uint32_t)C, p->k, &L);
+        if (L.smem <= (size_t)dev_smem) {
+            CL = cl;
+            NT = nt;
+            chosen = true;
+        }
+    }
+    if (!chosen)
+        return fail(SUCO_EUNSUPPORTED,
+                    "n=%lld with Ns=%d, C=%lld does not fit the shared memory of %s CTAs (SC-score planes too large)",
+                    (long long)ix->n, ix->Ns, (long long)C, p->cluster_size ? "the requested" : "up to 16");
     if (nq * CL > 0x7fffffffLL) return fail(SUCO_EINVAL, "too many queries in one call");
     QArgs& A = L.A;
     A.X = ix->X;

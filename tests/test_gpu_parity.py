@@ -184,12 +184,13 @@ def test_argument_errors_on_device(tiny):
 
 
 def test_score_array_too_large_is_reported():
-    # Ns collision bits per id must fit in the shared memory of at most 16 CTAs:
-    # 2M ids x 32 bits = 8 MB is beyond that
-    n = 2_000_000
+    # the sliced SC-score planes (bits(Ns)+1 bits per id) must fit in the shared
+    # memory of at most 16 CTAs: 8M ids x 7 bits is beyond that
+    n = 8_000_000
     dev = torch.device("cuda")
     X = torch.zeros((n, 64), device=dev)
     ix = pkg.suco_build_index(X, 32, 1, 0)
+    del X
     with pytest.raises(pkg.SucoError) as e:
         pkg.suco_query_batch(ix, torch.zeros((1, 64), device=dev), 10, 0.01, 0.001)
     assert e.value.code == -6
