@@ -160,6 +160,33 @@ SUCO_API int suco_export_index(const suco_index* index, float* centroids, uint32
  * an index of n points (host only). */
 SUCO_API int suco_thresholds(int64_t n, double alpha, double beta, int32_t k, int64_t* T, int64_t* C);
 
+/* K-means (Lloyd's algorithm) on one column range of a dataset, allocating
+ * nothing.  The paper has no counterpart: this is the same computation that
+ * suco_build_index runs for each half-subspace, offered to callers that cannot
+ * allocate device memory at the time they call it -- for example a process
+ * whose device memory is already handed out to its own allocator, or a caller
+ * under a latency budget that rules out cudaMalloc and the device
+ * synchronisation it implies.
+ *   data       (device) n x d FP32 row-major; columns [dim_off, dim_off+dim_len)
+ *              are clustered.
+ *   k          centroids, 1 <= k <= min(n, 256); dim_len <= 128.  Larger sizes
+ *              are rejected with SUCO_EUNSUPPORTED.
+ *   iters      Lloyd iterations (assignment, then member means; an empty
+ *              cluster keeps its centroid; ties go to the lowest index).
+ *   centroids  (device) k x dim_len FP32: the initial centroids on entry, the
+ *              final ones on return.
+ *   assign     (device) n int32: each point's nearest final centroid.
+ * The working sums and counts live in one fixed array of about 260 KB in
+ * device global memory, defined in the library and held by every GPU that
+ * loads it until the process exits.  All calls share that array: calls whose
+ * GPU work overlaps in time (other streams, other host threads) race on it.
+ * The first call on a device looks up the array's device address once; make
+ * that first call before any stream capture.  The call synchronises `stream`
+ * once (it reads back the data's largest magnitude to choose the fixed-point
+ * scale of the sums). */
+SUCO_API int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int32_t dim_off, int32_t dim_len,
+                                 int32_t k, int32_t iters, float* centroids, int32_t* assign, void* stream);
+
 /* Releases the index and its device memory.  NULL-safe. */
 SUCO_API void suco_free(suco_index* index);
 

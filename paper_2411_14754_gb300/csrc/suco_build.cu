@@ -12,6 +12,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "suco_internal.cuh"
@@ -333,3 +335,135 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
 }
 
 }  // namespace suco
+
+// ---------------------------------------------------------------------------
+// K-means on one column range without any allocation (suco_kmeans_noalloc).
+//
+// Some callers cannot allocate device memory while they run this step: a
+// process whose device memory is already handed out to its own allocator, or a
+// caller under a latency budget that rules out cudaMalloc and its implicit
+// device synchronisation.  For them, the centroid sums, counts and the
+// fixed-point scale live in one fixed array in device global memory, defined
+// here at file scope.  Every GPU that loads this library keeps the array
+// (NOALLOC_SCRATCH_BYTES) until the process exits.  Every call shares it, so
+// calls whose GPU work overlaps in time race on it.
+namespace suco {
+namespace {
+
+constexpr int NOALLOC_MAX_K = 256;    // centroids
+constexpr int NOALLOC_MAX_DIM = 128;  // dimensions of the column range
+constexpr size_t NOALLOC_SUM_BYTES = (size_t)NOALLOC_MAX_K * NOALLOC_MAX_DIM * 8;
+constexpr size_t NOALLOC_SCRATCH_BYTES = NOALLOC_SUM_BYTES + NOALLOC_MAX_K * 4 + 256;
+
+static __device__ __align__(256) unsigned char g_kmeans_scratch[NOALLOC_SCRATCH_BYTES];
+
+// host-side address of g_kmeans_scratch per device (the symbol's host name is
+// only a stand-in: kernels must be given this address)
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};
+
+int noalloc_scratch(int dev, unsigned char** out)
+{
+    if (dev < 0 || dev >= 256) return fail(SUCO_ESTATE, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_kmeans_scratch);
+        if (e != cudaSuccess)
+            return fail(SUCO_ECUDA, "cudaGetSymbolAddress of the K-means scratch failed: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    return SUCO_OK;
+}
+
+}  // namespace
+}  // namespace suco
+
+extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int32_t dim_off, int32_t dim_len,
+                                   int32_t k, int32_t iters, float* centroids, int32_t* assign, void* stream)
+{
+    using namespace suco;
+    clear_error();
+    if (!data || !centroids || !assign) return fail(SUCO_EINVAL, "data, centroids and assign must not be NULL");
+    if (n < 1 || n > 0x7fffffffLL) return fail(SUCO_EINVAL, "n=%lld must be in [1, 2^31-1]", (long long)n);
+    if (d < 1 || dim_off < 0 || dim_len < 1 || (int64_t)dim_off + dim_len > d)
+        return fail(SUCO_EINVAL, "columns [%d, %d) are not inside d=%d", dim_off, dim_off + dim_len, d);
+    if (k < 1 || k > n) return fail(SUCO_EINVAL, "k=%d must be in [1, n]", k);
+    if (iters < 0 || iters > 10000) return fail(SUCO_EINVAL, "iters=%d must be in [0, 10000]", iters);
+    if (k > NOALLOC_MAX_K || dim_len > NOALLOC_MAX_DIM)
+        return fail(SUCO_EUNSUPPORTED,
+                    "suco_kmeans_noalloc: k=%d, dim_len=%d exceed its fixed scratch (k <= %d, dim_len <= %d)", k,
+                    dim_len, NOALLOC_MAX_K, NOALLOC_MAX_DIM);
+    int dev = 0;
+    SUCO_CUDA_TRY(cudaGetDevice(&dev));
+    unsigned char* scratch = nullptr;
+    int rc = noalloc_scratch(dev, &scratch);
+    if (rc) return rc;
+    unsigned long long* gsum = reinterpret_cast<unsigned long long*>(scratch);
+    unsigned* gcnt = reinterpret_cast<unsigned*>(scratch + NOALLOC_SUM_BYTES);
+    unsigned* maxabs = gcnt + NOALLOC_MAX_K;
+    float* scale = reinterpret_cast<float*>(maxabs + 1);
+    float* inv_scale = scale + 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the column range as "half 0" of a one-subspace layout of width 2*dim_len
+    const float* Xc = data + dim_off;
+    const int32_t dd = 2 * dim_len, sub = 2 * dim_len;
+    int nsm = 0, smem_optin = 0;
+    SUCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SUCO_CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+
+    // fixed-point scale: max|x| * 2^S * n < 2^62
+    SUCO_CUDA_TRY(cudaMemsetAsync(maxabs, 0, 4, st));
+    maxabs_kernel<<<dim3(grid_for(n, 256, 1024), 1), 256, 0, st>>>(Xc, d, n, dd, 1, sub, maxabs);
+    SUCO_CUDA_TRY(cudaGetLastError());
+    unsigned mbits = 0;
+    SUCO_CUDA_TRY(cudaMemcpyAsync(&mbits, maxabs, 4, cudaMemcpyDeviceToHost, st));
+    SUCO_CUDA_TRY(cudaStreamSynchronize(st));
+    float m;
+    memcpy(&m, &mbits, 4);
+    int S = 0;
+    if (m > 0.f && std::isfinite(m)) {
+        int e;
+        std::frexp((double)m * (double)n, &e);
+        S = 61 - e;
+    }
+    S = std::max(-120, std::min(120, S));
+    const float sc[2] = {std::ldexp(1.0f, S), std::ldexp(1.0f, -S)};
+    SUCO_CUDA_TRY(cudaMemcpyAsync(scale, sc, 8, cudaMemcpyHostToDevice, st));
+
+    const size_t assign_smem = (size_t)k * dim_len * 4;
+    const size_t accum_smem = (size_t)k * dim_len * 8 + (size_t)k * 4;
+    const int use_smem = accum_smem <= (size_t)smem_optin ? 1 : 0;
+    // raise (never lower) the dynamic shared-memory limits of the shared kernels
+    cudaFuncAttributes fa;
+    SUCO_CUDA_TRY(cudaFuncGetAttributes(&fa, kmeans_assign_kernel));
+    if ((size_t)fa.maxDynamicSharedSizeBytes < assign_smem)
+        SUCO_CUDA_TRY(cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)assign_smem));
+    if (use_smem) {
+        SUCO_CUDA_TRY(cudaFuncGetAttributes(&fa, kmeans_accum_kernel));
+        if ((size_t)fa.maxDynamicSharedSizeBytes < accum_smem)
+            SUCO_CUDA_TRY(cudaFuncSetAttribute(kmeans_accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)accum_smem));
+    }
+    const dim3 g_assign(grid_for(n, 256, 8 * nsm), 1);
+    const dim3 g_accum(grid_for(n, 256, 2 * nsm), 1);
+    for (int it = 0; it < iters; ++it) {
+        kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign);
+        SUCO_CUDA_TRY(cudaGetLastError());
+        // sums and counts start from zero in every iteration (the array keeps the last call's contents)
+        SUCO_CUDA_TRY(cudaMemsetAsync(gsum, 0, (size_t)k * dim_len * 8, st));
+        SUCO_CUDA_TRY(cudaMemsetAsync(gcnt, 0, (size_t)k * 4, st));
+        kmeans_accum_kernel<<<g_accum, 256, use_smem ? accum_smem : 0, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, assign,
+                                                                             scale, gsum, gcnt, use_smem);
+        SUCO_CUDA_TRY(cudaGetLastError());
+        kmeans_finalize_kernel<<<dim3(grid_for((int64_t)k * dim_len, 256), 1), 256, 0, st>>>(
+            dd, 1, sub, k, dim_len, gsum, gcnt, inv_scale, centroids);
+        SUCO_CUDA_TRY(cudaGetLastError());
+    }
+    // the assignment against the final centroids
+    kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign);
+    SUCO_CUDA_TRY(cudaGetLastError());
+    return SUCO_OK;
+}

@@ -64,11 +64,13 @@ def load_library():
     L.suco_index_get_info.argtypes = [vp, C.POINTER(_IndexInfo)]
     L.suco_export_index.argtypes = [vp, vp, vp, vp]
     L.suco_thresholds.argtypes = [i64, f64, f64, i32, C.POINTER(i64), C.POINTER(i64)]
+    L.suco_kmeans_noalloc.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, vp]
     L.suco_free.argtypes = [vp]
     L.suco_free.restype = None
     L.suco_last_error.restype = C.c_char_p
     for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_query_batch", "suco_query_debug",
-                 "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version"):
+                 "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version",
+                 "suco_kmeans_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -204,6 +206,25 @@ def suco_thresholds(n: int, alpha: float, beta: float, k: int):
     T, Cc = C.c_int64(), C.c_int64()
     _check(load_library().suco_thresholds(int(n), float(alpha), float(beta), int(k), C.byref(T), C.byref(Cc)))
     return T.value, Cc.value
+
+
+def suco_kmeans_noalloc(data: torch.Tensor, dim_off: int, dim_len: int, centroids: torch.Tensor, iters: int,
+                        assign: torch.Tensor = None, stream=None):
+    """Lloyd K-means on columns [dim_off, dim_off+dim_len) of ``data`` without any
+    device allocation inside the library.  ``centroids`` (k x dim_len float32
+    CUDA tensor) holds the initial centroids and receives the final ones;
+    returns the int32 assignment (written into ``assign`` if given)."""
+    _dev_f32(data, "data")
+    _dev_f32(centroids, "centroids")
+    n, d = data.shape
+    k = centroids.shape[0]
+    if centroids.shape[1] != dim_len:
+        raise ValueError("centroids must be k x dim_len")
+    if assign is None:
+        assign = torch.empty(n, dtype=torch.int32, device=data.device)
+    _check(load_library().suco_kmeans_noalloc(_ptr(data), n, d, dim_off, dim_len, k, iters, _ptr(centroids),
+                                              _ptr(assign), _stream(stream)))
+    return assign
 
 
 def suco_free(index: SucoIndex):
