@@ -101,14 +101,27 @@ SUCO_API int suco_build_index_from_assignments(const float* data, int64_t n, int
                                       const float* centroids, const int32_t* assign, void* stream,
                                       suco_index** out);
 
-/* Query parameters (Algorithm 4). */
+/* Query parameters (Algorithm 4).  The three per-query arrays are optional;
+ * a query without an array entry uses the scalar.  With per-query values the
+ * thresholds are computed per query on the device by the same formula: T_b
+ * from alpha_b, C_b from beta_b and k_b.  The scalar beta is an upper bound:
+ * it sizes the candidate storage, and C_b never exceeds C(beta, k).  A
+ * per-query k_b < k leaves result columns k_b..k-1 padded (-1, +inf). */
+/* suco_query_params.flags: by default the grid holds as many clusters as fit
+ * on the GPU at once and each cluster answers its share of the batch in turn;
+ * this flag launches one cluster per query instead. */
+#define SUCO_QUERY_ONE_CLUSTER_PER_QUERY 1
+
 typedef struct suco_query_params {
-    int32_t k;            /* results per query, 1..256                                  */
+    int32_t k;            /* results per query (the maximum if k_per_query), 1..256   */
     int32_t cluster_size; /* CTAs cooperating on one query (1,2,4,8,16); 0 = automatic  */
     double alpha;         /* collision ratio, 0 < alpha <= 1                            */
-    double beta;          /* re-rank ratio,   0 < beta  <= 1                            */
+    double beta;          /* re-rank ratio,   0 < beta  <= 1 (bound of beta_per_query)   */
     int32_t threads;      /* threads per CTA (512 or 1024); 0 = automatic               */
-    int32_t reserved0;    /* must be 0                                                  */
+    int32_t flags;        /* SUCO_QUERY_* bits, 0 by default                            */
+    const int32_t* k_per_query;    /* (device, nullable) [nq], clamped to [1, k]        */
+    const float* alpha_per_query;  /* (device, nullable) [nq], clamped to (0, 1]        */
+    const float* beta_per_query;   /* (device, nullable) [nq], clamped to (0, beta]     */
 } suco_query_params;
 
 /* Answers nq queries (Algorithm 4; Algorithm 3 for the cell walk).
@@ -136,6 +149,14 @@ typedef struct suco_query_debug_out {
 /* suco_query_batch plus the per-stage outputs above (same arguments). */
 SUCO_API int suco_query_debug(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
                      int32_t* out_ids, float* out_dist, const suco_query_debug_out* debug, void* stream);
+
+/* Times every launch shape (cluster size x threads per CTA) that fits, on the
+ * given queries and parameters (which must leave cluster_size and threads at
+ * 0), and remembers the fastest in the index: later calls with the same k and
+ * candidate bound C and automatic shape use it.  Returns the chosen shape.
+ * Synchronous; allocates two nq x k scratch outputs for the timing runs. */
+SUCO_API int suco_autotune(suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
+                           void* stream, int32_t* cluster_size, int32_t* threads);
 
 /* Sizes of an index. */
 typedef struct suco_index_info {

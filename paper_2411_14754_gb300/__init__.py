@@ -3,6 +3,6 @@
 The query path runs in hand-written CUDA kernels for sm_103a behind the C ABI
 of ``include/suco.h``; ``paper_2411_14754_gb300.suco`` is its Python binding.
 """
-from .suco import (SucoError, SucoIndex, load_library, suco_build_index, suco_build_index_from_assignments,  # noqa: F401
+from .suco import (SucoError, SucoIndex, load_library, suco_autotune, suco_build_index, suco_build_index_from_assignments,  # noqa: F401
                    suco_export_index, suco_free, suco_index_get_info, suco_kmeans_noalloc, suco_last_error, suco_query_batch,
                    suco_query_debug, suco_thresholds, suco_version)

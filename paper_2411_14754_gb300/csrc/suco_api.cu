@@ -139,7 +139,7 @@ int check_query_params(const suco_index* index, const float* queries, int64_t nq
     if (p->k < 1 || p->k > 256) return fail(SUCO_EINVAL, "k=%d must be in [1, 256]", p->k);
     if (!(p->alpha > 0.0 && p->alpha <= 1.0)) return fail(SUCO_EINVAL, "alpha=%g must be in (0, 1]", p->alpha);
     if (!(p->beta > 0.0 && p->beta <= 1.0)) return fail(SUCO_EINVAL, "beta=%g must be in (0, 1]", p->beta);
-    if (p->reserved0 != 0) return fail(SUCO_EINVAL, "reserved0 must be 0");
+    if (p->flags & ~SUCO_QUERY_ONE_CLUSTER_PER_QUERY) return fail(SUCO_EINVAL, "unknown flags 0x%x", p->flags);
     if (nq > 0 && (!queries || !ids || !dist)) return fail(SUCO_EINVAL, "queries/out_ids/out_dist must not be NULL");
     return SUCO_OK;
 }
@@ -264,6 +264,63 @@ int suco_query_debug(const suco_index* index, const float* queries, int64_t nq, 
     int rc = check_query_params(index, queries, nq, params, out_ids, out_dist);
     if (rc) return rc;
     return launch_query(&index->ix, queries, nq, params, out_ids, out_dist, debug, (cudaStream_t)stream);
+}
+
+int suco_autotune(suco_index* index, const float* queries, int64_t nq, const suco_query_params* params, void* stream,
+                  int32_t* cluster_size, int32_t* threads)
+{
+    clear_error();
+    if (!index || !queries || !params || nq < 1) return fail(SUCO_EINVAL, "index, queries, params and nq >= 1 required");
+    if (params->cluster_size || params->threads) return fail(SUCO_EINVAL, "autotune needs cluster_size = threads = 0");
+    int rc = check_query_params(index, queries, nq, params, (const int32_t*)queries, queries);
+    if (rc) return rc;
+    DeviceIndex& ix = index->ix;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf ids, dist;
+    if (ids.alloc((size_t)nq * params->k * 4) || dist.alloc((size_t)nq * params->k * 4)) return SUCO_ENOMEM;
+    cudaEvent_t e0, e1;
+    SUCO_CUDA_TRY(cudaEventCreate(&e0));
+    SUCO_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best_cl = 0, best_nt = 0;
+    const int cls[] = {1, 2, 4, 8, 16}, nts[] = {512, 1024};
+    for (int cl : cls)
+        for (int nt : nts) {
+            suco_query_params q = *params;
+            q.cluster_size = cl;
+            q.threads = nt;
+            if (launch_query(&ix, queries, nq, &q, ids.as<int32_t>(), dist.as<float>(), nullptr, st) != SUCO_OK) {
+                cudaGetLastError();
+                continue;  // this shape does not fit
+            }
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 3; ++rep)
+                launch_query(&ix, queries, nq, &q, ids.as<int32_t>(), dist.as<float>(), nullptr, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail(SUCO_ECUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_cl = cl;
+                best_nt = nt;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!best_cl) return fail(SUCO_EUNSUPPORTED, "no launch shape fits this index and these parameters");
+    int64_t T = 0, C = 0;
+    thresholds(ix.n, params->alpha, params->beta, params->k, &T, &C);
+    for (auto it = ix.tuned.begin(); it != ix.tuned.end();)
+        it = (it->k == params->k && it->C == (uint32_t)C) ? ix.tuned.erase(it) : it + 1;
+    ix.tuned.push_back({params->k, (uint32_t)C, best_cl, best_nt});
+    if (cluster_size) *cluster_size = best_cl;
+    if (threads) *threads = best_nt;
+    return SUCO_OK;
 }
 
 int suco_index_get_info(const suco_index* index, suco_index_info* info)

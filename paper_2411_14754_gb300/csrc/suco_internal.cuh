@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "suco.h"
 
@@ -33,6 +34,14 @@ struct DeviceIndex {
     uint32_t* split = nullptr;    // [Ns][NCH+1][K] absolute position in perm[i] where chunk j starts in cell x
     int device = 0;
     int64_t bytes = 0;
+    // launch shapes chosen by suco_autotune, per (k, candidate bound C)
+    struct Tuned {
+        int32_t k;
+        uint32_t C;
+        int32_t CL;
+        int32_t NT;
+    };
+    std::vector<Tuned> tuned;
 };
 
 // Half-subspace geometry (Definition 3 contiguous case; Algorithm 2 halves).

@@ -1,5 +1,7 @@
 // The SuCo query path (Section 4.2: Algorithm 4, with Algorithm 3's cell walk)
-// as one kernel in which a thread-block cluster of CL CTAs answers one query.
+// as one kernel in which a thread-block cluster of CL CTAs answers one query at
+// a time; the grid holds as many clusters as fit on the GPU at once and each
+// cluster loops over its share of the batch.
 //
 // Stages inside the kernel (one launch, no global scratch):
 //   S0  the query row is staged in shared memory.
@@ -38,6 +40,8 @@
 //       lists by rank.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "suco_internal.cuh"
 
@@ -67,7 +71,11 @@ struct QArgs {
     const float* __restrict__ Q;
     int64_t nq;
     int32_t k, k_pad;
-    uint32_t T, C, per_cta;
+    uint32_t T, C, per_cta;  // scalar thresholds; C and per_cta are also the bounds of per-query values
+    double alpha, beta;
+    const int32_t* k_per;    // optional per-query k, alpha, beta
+    const float* alpha_per;
+    const float* beta_per;
     uint32_t span, G;  // ids per CTA, 32-id groups per CTA
     uint32_t nbits;    // B: bit planes of the sliced SC-score counts
     int32_t* out_ids;
@@ -239,7 +247,7 @@ __device__ __forceinline__ int value_bucket(float s, float smin, float scale)
 
 // S1-S3 for subspace i of query b (the CTA that owns i).
 template <int NT>
-__device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
+__device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint32_t T)
 {
     const int sk = A.sqrtK;
     const int lane = threadIdx.x & 31;
@@ -346,7 +354,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
 #pragma unroll
         for (int u = 0; u < BPT; ++u) {
             const int e = threadIdx.x * BPT + u;
-            if (e < NB && run < A.T && run + v[u] >= A.T) {
+            if (e < NB && run < T && run + v[u] >= T) {
                 bc[3] = (unsigned long long)e;
                 bc[4] = run;
             }
@@ -404,7 +412,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
                 const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            const uint32_t need = (uint32_t)(A.T - below);
+            const uint32_t need = (uint32_t)(T - below);
             const uint32_t hit = __ballot_sync(0xffffffffu, incl >= need && lane < (int)nm);
             const int src = __ffs(hit) - 1;
             const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
@@ -484,7 +492,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i)
                 if (lane >= o) incl += y;
             }
             const uint32_t excl = incl - s;
-            const uint32_t need = (uint32_t)(A.T - below);
+            const uint32_t need = (uint32_t)(T - below);
             if (excl < need && incl >= need) {
                 uint32_t cum = excl;
                 int bin = lane * 8 + 7;
@@ -692,10 +700,37 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     constexpr int NC = NSMAX + 2;  // count slots: [0] = valid ids, [s] = #scores >= s
     const uint32_t r = cluster_rank();
     const int CL = A.CL;
-    const int64_t b = blockIdx.x / CL;
+    // persistent clusters: cluster c answers queries c, c + G, c + 2G, ... (G clusters in the grid)
+    for (int64_t b = blockIdx.x / CL; b < A.nq; b += gridDim.x / CL) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // ---- S0: stage the query; clear the published counts and candidate slots
+    // ---- S0: this query's thresholds; stage the query; clear the published
+    // counts and candidate slots
+    uint32_t* qpar = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 110;  // T, C, k, per_cta
+    if (threadIdx.x == 0) {
+        uint32_t kq = (uint32_t)A.k, T = A.T, C = A.C;
+        if (A.k_per) kq = (uint32_t)min(max(A.k_per[b], 1), A.k);
+        if (A.alpha_per) {
+            double a = (double)A.alpha_per[b];
+            a = a > 0.0 ? fmin(a, 1.0) : 0.0;  // NaN and non-positive values give T = 1
+            double t = ceil(a * (double)A.n - 1e-9);
+            T = (uint32_t)fmin(fmax(t, 1.0), (double)A.n);
+        }
+        if (A.beta_per || A.k_per) {
+            double be = A.beta;
+            if (A.beta_per) {
+                const double v = (double)A.beta_per[b];
+                be = v > 0.0 ? fmin(v, A.beta) : A.beta;
+            }
+            double c = fmax(ceil(be * (double)A.n - 1e-9), (double)kq);
+            c = fmin(fmax(c, 1.0), (double)A.n);
+            C = min((uint32_t)c, A.C);
+        }
+        qpar[0] = T;
+        qpar[1] = C;
+        qpar[2] = kq;
+        qpar[3] = (C + CL - 1) / CL;
+    }
     {
         float* qs = reinterpret_cast<float*>(smem + A.o_q);
         const float* qg = A.Q + b * A.d;
@@ -707,8 +742,9 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     }
     __syncthreads();
 
+    const uint32_t qT = qpar[0], qC = qpar[1], qk = qpar[2], qper = qpar[3];
     // ---- S1-S3 for the subspaces this CTA owns
-    for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT>(A, smem, b, i);
+    for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT>(A, smem, b, i, qT);
     // clear the bit planes (the union region served as S3 scratch)
     {
         uint4* pw = reinterpret_cast<uint4*>(smem + A.o_union);
@@ -807,7 +843,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         for (int s = A.Ns; s >= 1; --s) {
             uint32_t tot = 0;
             for (int rr = 0; rr < CL; ++rr) tot += allc[rr * NC + s];
-            if (tot >= A.C) {
+            if (tot >= qC) {
                 theta = s;
                 break;
             }
@@ -835,7 +871,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         }
         sel[0] = (uint32_t)theta;
         sel[1] = n_gt;
-        sel[2] = A.C - n_gt;
+        sel[2] = qC - n_gt;
     }
     __syncthreads();
     {
@@ -884,9 +920,9 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
                 gm &= ~bit;
                 em &= ~bit;
                 if (pos != 0xffffffffu) {
-                    const uint32_t owner = pos / A.per_cta;
+                    const uint32_t owner = pos / qper;
                     const uint32_t id = base_id + (uint32_t)j;
-                    st_cluster_u32(slot_base[owner] + 4u * (pos - owner * A.per_cta), id);
+                    st_cluster_u32(slot_base[owner] + 4u * (pos - owner * qper), id);
                     if (A.dbg_cands) A.dbg_cands[b * A.C + pos] = (int32_t)id;
                 }
             }
@@ -898,7 +934,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
 
     // ---- S6: exact FP32 re-rank of this CTA's share of the candidates
     const uint32_t* slots = reinterpret_cast<const uint32_t*>(smem + A.o_slots);
-    const uint32_t mine = A.C > r * A.per_cta ? min(A.per_cta, A.C - r * A.per_cta) : 0u;
+    const uint32_t mine = qC > r * qper ? min(qper, qC - r * qper) : 0u;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + A.o_keys);  // [sortP]
     const int ld4 = (int)(A.ld / 4);
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
@@ -956,7 +992,8 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     uint32_t* khist = reinterpret_cast<uint32_t*>(smem + A.o_union);               // [NB]
     unsigned long long* surv = reinterpret_cast<unsigned long long*>(khist + NB);   // [SURV_CAP]
     uint32_t* kv = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 100;             // min, max, bucket, count
-    const uint32_t k = (uint32_t)A.k;
+    const uint32_t k = qk;           // this query's k (lists are stored at stride A.k)
+    const uint32_t kst = (uint32_t)A.k;
     unsigned long long* best = keys;  // sorted top-k ends up here
     uint32_t nbest = 0;
     if (mine <= 2 * k || mine <= 64) {
@@ -1111,18 +1148,19 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
                 rank += lo;
             }
             if (rank < k) {
-                A.out_ids[b * k + rank] = (int32_t)(uint32_t)(v & 0xffffffffu);
-                A.out_dist[b * k + rank] = __uint_as_float((uint32_t)(v >> 32));
+                A.out_ids[b * kst + rank] = (int32_t)(uint32_t)(v & 0xffffffffu);
+                A.out_dist[b * kst + rank] = __uint_as_float((uint32_t)(v >> 32));
             }
         }
         if (real) atomicAdd(nreal, real);
         __syncthreads();
-        // fewer than k real keys in total: pad the tail
-        for (uint32_t t = *nreal + threadIdx.x; t < k; t += NT) {
-            A.out_ids[b * k + t] = -1;
-            A.out_dist[b * k + t] = __int_as_float(0x7f800000);
+        // fewer than k real keys, or a per-query k below the row length: pad the tail
+        for (uint32_t t = min(*nreal, k) + threadIdx.x; t < kst; t += NT) {
+            A.out_ids[b * kst + t] = -1;
+            A.out_dist[b * kst + t] = __int_as_float(0x7f800000);
         }
     }
+    }  // next query: the cluster barriers of its stages order every remote access
 }
 
 uint32_t align16(uint64_t x) { return (uint32_t)((x + 15) & ~uint64_t(15)); }
@@ -1186,15 +1224,24 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, in
     return SUCO_OK;
 }
 
+// Co-resident clusters for a launch shape, cached (the occupancy query is not
+// repeated, so later calls can be captured into a CUDA graph).
+struct OccKey {
+    const void* fn;
+    int CL;
+    size_t smem;
+};
+std::mutex g_occ_mu;
+std::vector<std::pair<OccKey, int>> g_occ;
+
 template <int NT, int NSMAX>
-int launch_t(const Layout& L, int64_t nq, cudaStream_t st)
+int launch_t(const Layout& L, int64_t nq, bool persistent, cudaStream_t st)
 {
     auto kern = suco_query_kernel<NT, NSMAX>;
     SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     if (L.A.CL > 8) SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3((unsigned)(nq * L.A.CL), 1, 1);
     cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = L.smem;
     cfg.stream = st;
@@ -1205,6 +1252,28 @@ int launch_t(const Layout& L, int64_t nq, cudaStream_t st)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    int64_t G = nq;
+    if (persistent) {
+        int nclusters = 0;
+        {
+            std::lock_guard<std::mutex> lock(g_occ_mu);
+            for (auto& e : g_occ)
+                if (e.first.fn == (const void*)kern && e.first.CL == L.A.CL && e.first.smem == L.smem)
+                    nclusters = e.second;
+        }
+        if (nclusters == 0) {
+            cfg.gridDim = dim3((unsigned)L.A.CL, 1, 1);
+            if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+                cudaGetLastError();
+                nclusters = 0;
+            } else {
+                std::lock_guard<std::mutex> lock(g_occ_mu);
+                g_occ.push_back({OccKey{(const void*)kern, L.A.CL, L.smem}, nclusters});
+            }
+        }
+        if (nclusters > 0) G = std::min<int64_t>(nq, nclusters);
+    }
+    cfg.gridDim = dim3((unsigned)(G * L.A.CL), 1, 1);
     SUCO_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, L.A));
     return SUCO_OK;
 }
@@ -1221,6 +1290,12 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     int NT = p->threads;
     if (NT != 0 && NT != 512 && NT != 1024) return fail(SUCO_EINVAL, "threads must be 0, 512 or 1024 (got %d)", NT);
     int CL = p->cluster_size;
+    if (CL == 0 && NT == 0)
+        for (const auto& t : ix->tuned)
+            if (t.k == p->k && t.C == (uint32_t)C) {
+                CL = t.CL;
+                NT = t.NT;
+            }
     if (CL != 0 && CL != 1 && CL != 2 && CL != 4 && CL != 8 && CL != 16)
         return fail(SUCO_EINVAL, "cluster_size must be 0, 1, 2, 4, 8 or 16 (got %d)", CL);
     int dev_smem = 0, sm_smem = 0, reserved = 0;
@@ -1274,6 +1349,11 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     A.nq = nq;
     A.T = (uint32_t)T;
     A.C = (uint32_t)C;
+    A.alpha = p->alpha;
+    A.beta = p->beta;
+    A.k_per = p->k_per_query;
+    A.alpha_per = p->alpha_per_query;
+    A.beta_per = p->beta_per_query;
     A.out_ids = ids;
     A.out_dist = dist;
     if (dbg) {
@@ -1283,14 +1363,15 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
         A.dbg_scores = dbg->scores;
         A.dbg_cands = dbg->cands;
     }
+    const bool persistent = (p->flags & SUCO_QUERY_ONE_CLUSTER_PER_QUERY) == 0;
     if (NT == 1024) {
-        if (nsmax == 8) return launch_t<1024, 8>(L, nq, st);
-        if (nsmax == 16) return launch_t<1024, 16>(L, nq, st);
-        return launch_t<1024, 32>(L, nq, st);
+        if (nsmax == 8) return launch_t<1024, 8>(L, nq, persistent, st);
+        if (nsmax == 16) return launch_t<1024, 16>(L, nq, persistent, st);
+        return launch_t<1024, 32>(L, nq, persistent, st);
     }
-    if (nsmax == 8) return launch_t<512, 8>(L, nq, st);
-    if (nsmax == 16) return launch_t<512, 16>(L, nq, st);
-    return launch_t<512, 32>(L, nq, st);
+    if (nsmax == 8) return launch_t<512, 8>(L, nq, persistent, st);
+    if (nsmax == 16) return launch_t<512, 16>(L, nq, persistent, st);
+    return launch_t<512, 32>(L, nq, persistent, st);
 }
 
 }  // namespace suco

@@ -29,7 +29,8 @@ class _BuildParams(C.Structure):
 
 class _QueryParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("cluster_size", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
-                ("threads", C.c_int32), ("reserved0", C.c_int32)]
+                ("threads", C.c_int32), ("flags", C.c_int32), ("k_per_query", C.c_void_p),
+                ("alpha_per_query", C.c_void_p), ("beta_per_query", C.c_void_p)]
 
 
 class _DebugOut(C.Structure):
@@ -65,12 +66,13 @@ def load_library():
     L.suco_export_index.argtypes = [vp, vp, vp, vp]
     L.suco_thresholds.argtypes = [i64, f64, f64, i32, C.POINTER(i64), C.POINTER(i64)]
     L.suco_kmeans_noalloc.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, vp]
+    L.suco_autotune.argtypes = [vp, vp, i64, C.POINTER(_QueryParams), vp, C.POINTER(i32), C.POINTER(i32)]
     L.suco_free.argtypes = [vp]
     L.suco_free.restype = None
     L.suco_last_error.restype = C.c_char_p
     for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_query_batch", "suco_query_debug",
                  "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version",
-                 "suco_kmeans_noalloc"):
+                 "suco_kmeans_noalloc", "suco_autotune"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -144,21 +146,38 @@ def suco_build_index_from_assignments(data: torch.Tensor, Ns: int, sqrtK: int, c
     return SucoIndex(h)
 
 
-def _qparams(k, alpha, beta, cluster_size, threads):
-    return _QueryParams(int(k), int(cluster_size), float(alpha), float(beta), int(threads), 0)
+def _per_query(t, dtype, nq, name):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() == nq):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of {nq} {dtype}")
+    return t.data_ptr()
+
+
+QUERY_ONE_CLUSTER_PER_QUERY = 1
+
+
+def _qparams(k, alpha, beta, cluster_size, threads, nq=0, k_per_query=None, alpha_per_query=None,
+             beta_per_query=None, flags=0):
+    return _QueryParams(int(k), int(cluster_size), float(alpha), float(beta), int(threads), int(flags),
+                        _per_query(k_per_query, torch.int32, nq, "k_per_query"),
+                        _per_query(alpha_per_query, torch.float32, nq, "alpha_per_query"),
+                        _per_query(beta_per_query, torch.float32, nq, "beta_per_query"))
 
 
 def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
                      out_ids: Optional[torch.Tensor] = None, out_dist: Optional[torch.Tensor] = None,
-                     cluster_size: int = 0, threads: int = 0, stream=None):
-    """Algorithm 4 for every row of ``queries``; returns (ids int32 [nq,k], squared dists float32 [nq,k])."""
+                     cluster_size: int = 0, threads: int = 0, stream=None, k_per_query=None, alpha_per_query=None,
+                     beta_per_query=None, flags: int = 0):
+    """Algorithm 4 for every row of ``queries``; returns (ids int32 [nq,k], squared dists float32 [nq,k]).
+    Optional per-query CUDA tensors: k_per_query (int32), alpha_per_query, beta_per_query (float32)."""
     _dev_f32(queries, "queries")
     nq = queries.shape[0]
     if out_ids is None:
         out_ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
-    p = _qparams(k, alpha, beta, cluster_size, threads)
+    p = _qparams(k, alpha, beta, cluster_size, threads, nq, k_per_query, alpha_per_query, beta_per_query, flags)
     _check(load_library().suco_query_batch(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out_ids),
                                            _ptr(out_dist), _stream(stream)))
     return out_ids, out_dist
@@ -166,7 +185,7 @@ def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
 
 def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
                      cluster_size: int = 0, threads: int = 0, want=("t_eff", "activated", "dtab", "scores", "cands"),
-                     stream=None):
+                     stream=None, k_per_query=None, alpha_per_query=None, beta_per_query=None, flags: int = 0):
     """suco_query_batch plus per-stage outputs; returns a dict of CUDA tensors."""
     _dev_f32(queries, "queries")
     nq = queries.shape[0]
@@ -182,11 +201,24 @@ def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
         out[name] = torch.full(shp, -1 if dt != torch.uint8 else 255, dtype=dt, device=dev)
     dbg = _DebugOut(*[(out[n].data_ptr() if n in out else None) for n in ("t_eff", "activated", "dtab", "scores",
                                                                         "cands")])
-    p = _qparams(k, alpha, beta, cluster_size, threads)
+    p = _qparams(k, alpha, beta, cluster_size, threads, nq, k_per_query, alpha_per_query, beta_per_query, flags)
     _check(load_library().suco_query_debug(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out["ids"]),
                                            _ptr(out["dist"]), C.byref(dbg), _stream(stream)))
     out["T"], out["C"] = T, Cc
     return out
+
+
+def suco_autotune(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float, stream=None,
+                  k_per_query=None, alpha_per_query=None, beta_per_query=None, flags: int = 0):
+    """Time every launch shape on these queries; the index remembers the fastest.
+    Returns (cluster_size, threads)."""
+    _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    p = _qparams(k, alpha, beta, 0, 0, nq, k_per_query, alpha_per_query, beta_per_query, flags)
+    cl, nt = C.c_int32(), C.c_int32()
+    _check(load_library().suco_autotune(index.handle, _ptr(queries), nq, C.byref(p), _stream(stream), C.byref(cl),
+                                        C.byref(nt)))
+    return cl.value, nt.value
 
 
 def suco_index_get_info(index: SucoIndex) -> dict:

@@ -25,14 +25,15 @@ def built():
     pkg.load_library()
 
 
-def run(X, idx_o, Q, k, alpha, beta, cluster_size=0, threads=0, stages=True, want=None, sample=None):
+def run(X, idx_o, Q, k, alpha, beta, cluster_size=0, threads=0, stages=True, want=None, sample=None, flags=0):
     dev = torch.device("cuda")
     Xd = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
     Qd = torch.from_numpy(np.ascontiguousarray(Q)).to(dev)
     ix = pkg.suco_build_index_from_assignments(Xd, idx_o["Ns"], idx_o["sqrtK"], idx_o["centroids"], idx_o["assign"])
     try:
         want = want or (("t_eff", "activated", "dtab", "scores", "cands") if stages else ())
-        out = pkg.suco_query_debug(ix, Qd, k, alpha, beta, cluster_size=cluster_size, threads=threads, want=want)
+        out = pkg.suco_query_debug(ix, Qd, k, alpha, beta, cluster_size=cluster_size, threads=threads, want=want,
+                                   flags=flags)
         torch.cuda.synchronize()
         host = {kk: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for kk, v in out.items()}
     finally:
@@ -61,10 +62,11 @@ def test_tiny_workload_all_queries(tiny):
 
 
 @pytest.mark.parametrize("cluster_size", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("threads", [512, 1024])
-def test_tiny_workload_every_launch_shape(tiny, cluster_size, threads):
+def test_tiny_workload_every_launch_shape(tiny, cluster_size, threads, flags):
     w, X, Q, idx = tiny
-    run(X, idx, Q[:24], w.k, w.alpha, w.beta, cluster_size=cluster_size, threads=threads)
+    run(X, idx, Q[:24], w.k, w.alpha, w.beta, cluster_size=cluster_size, threads=threads, flags=flags)
 
 
 @pytest.mark.parametrize("alpha,beta,k", [(0.01, 0.001, 10), (0.2, 0.02, 50), (1.0, 0.005, 10), (0.05, 1.0, 7),
@@ -194,4 +196,99 @@ def test_score_array_too_large_is_reported():
     with pytest.raises(pkg.SucoError) as e:
         pkg.suco_query_batch(ix, torch.zeros((1, 64), device=dev), 10, 0.01, 0.001)
     assert e.value.code == -6
+    pkg.suco_free(ix)
+
+
+def test_per_query_k_alpha_beta(tiny):
+    # a mixed batch: every query has its own k, alpha and beta (device arrays); the
+    # scalar beta bounds the per-query values
+    w, X, Q, idx = tiny
+    rng = np.random.default_rng(77)
+    nq = 48
+    ks = rng.choice([1, 10, 37], nq).astype(np.int32)
+    al = rng.choice([0.01, 0.03, 0.05, 0.2], nq).astype(np.float32)
+    be = rng.choice([0.001, 0.003, 0.005, 0.02, 0.5], nq).astype(np.float32)
+    kmax, beta_bound = 37, 0.02
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    try:
+        out = pkg.suco_query_debug(ix, torch.from_numpy(Q[:nq]).to(dev), kmax, 0.05, beta_bound,
+                                   k_per_query=torch.from_numpy(ks).to(dev),
+                                   alpha_per_query=torch.from_numpy(al).to(dev),
+                                   beta_per_query=torch.from_numpy(be).to(dev))
+        torch.cuda.synchronize()
+        host = {kk: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for kk, v in out.items()}
+    finally:
+        pkg.suco_free(ix)
+    n = X.shape[0]
+    for b in range(nq):
+        kb = int(ks[b])
+        T = oracle.collision_threshold(float(al[b]), n)
+        C = oracle.candidate_count(min(float(be[b]), beta_bound), n, kb)
+        o = oracle.query(X, idx, Q[b], kb, T, C, rank_precision=1)
+        np.testing.assert_array_equal(host["t_eff"][b], o["teff"])
+        np.testing.assert_array_equal(host["scores"][b].astype(np.int32), o["scores"])
+        assert sorted(host["cands"][b][:C].tolist()) == sorted(o["cands"].tolist())
+        from parity_util import assert_topk_matches
+        assert_topk_matches(X, Q[b], host["ids"][b][:kb], host["dist"][b][:kb], o["ids"], o["dist"])
+        assert (host["ids"][b][kb:] == -1).all() and np.isinf(host["dist"][b][kb:]).all()
+
+
+def test_one_cluster_per_query_flag(tiny):
+    w, X, Q, idx = tiny
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    Qd = torch.from_numpy(Q).to(dev)
+    a = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)
+    b = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta, flags=pkg.suco.QUERY_ONE_CLUSTER_PER_QUERY)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    pkg.suco_free(ix)
+    host = run(X, idx, Q[:16], w.k, w.alpha, w.beta)  # persistent path against the oracle already covered
+    assert host["ids"].shape == (16, w.k)
+
+
+def test_autotune_picks_a_shape_with_identical_results(tiny):
+    w, X, Q, idx = tiny
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    Qd = torch.from_numpy(Q).to(dev)
+    ref = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta, cluster_size=1, threads=512)
+    cl, nt = pkg.suco_autotune(ix, Qd, w.k, w.alpha, w.beta)
+    assert cl in (1, 2, 4, 8, 16) and nt in (512, 1024)
+    got = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)
+    torch.cuda.synchronize()
+    assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
+    pkg.suco_free(ix)
+
+
+def test_query_replays_from_a_cuda_graph(tiny):
+    w, X, Q, idx = tiny
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    Qd = torch.from_numpy(Q[:32]).to(dev)
+    ids = torch.empty((32, w.k), dtype=torch.int32, device=dev)
+    dist = torch.empty((32, w.k), dtype=torch.float32, device=dev)
+    ref = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)  # first call outside capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta, out_ids=ids, out_dist=dist, stream=s)
+    for rep in range(3):
+        ids.fill_(-7)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(ids, ref[0]) and torch.equal(dist, ref[1])
+    # replay on new inputs written into the captured buffer
+    Qd.copy_(torch.from_numpy(Q[32:64]).to(dev))
+    g.replay()
+    ref2 = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)
+    torch.cuda.synchronize()
+    assert torch.equal(ids, ref2[0])
     pkg.suco_free(ix)
