@@ -2,13 +2,20 @@
 
 A step is one batch of queries through the whole query path (centroid
 distances, cell activation, SC-score counting, candidate selection, exact
-re-rank, top-k: one kernel launch).  Default workload: 1,000,000 SIFT-like
-points (d=128, integer features 0..255), Ns=8, sqrtK=50, alpha=0.05,
-beta=0.005, k=50, 10,000 queries in batches of 1024.  The index is built on
-the GPU beforehand; queries are resident in device memory for the timed
-value and copied from pinned host memory for the end-to-end figure.
+re-rank, top-k).  Default workload: 1,000,000 points, d=256, drawn from a hard
+Gaussian mixture (2000 components, sigma log-uniform in [0.5, 8], 10% uniform
+noise), Ns=16, sqrtK=50, k=10, 10,000 evaluation queries in batches of 1024.
+There the ratio network (trained first on this GPU from plain-SuCo labels on
+200,000 training queries) predicts each query's alpha and beta: a step is one
+predict launch and one query launch.  Both the learned arm and the plain
+fixed-ratio arm are timed at their fastest operating point whose mean
+recall@10 reaches 0.95 on the evaluation queries.  Other workloads
+(--workload 1..4) time the plain path at the workload's own alpha and beta.
+The index is built on the GPU beforehand; queries are resident in device
+memory for the timed value and copied from pinned host memory for the
+end-to-end figure.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 5] [--impl reference]
 
 Prints one JSON line (rank 0).  With N > 1 (launched by torchrun) every rank
 holds its own index replica and answers its own query batches (no data-path
@@ -37,7 +44,10 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--workload", type=int, default=2)
+    p.add_argument("--workload", type=int, default=5)
+    p.add_argument("--n-train", type=int, default=0, help="training queries of the ratio network "
+                   "(0: the workload's own count)")
+    p.add_argument("--target-recall", type=float, default=0.95)
     p.add_argument("--impl", default="suco", choices=["suco", "reference"])
     p.add_argument("--cluster-size", type=int, default=0)
     p.add_argument("--threads", type=int, default=0)
@@ -137,10 +147,12 @@ def algorithmic_bytes_per_query(w, T, C, teff_mean_total):
     return 4.0 * teff_mean_total + 4.0 * C * w.d
 
 
-def run_cpu_baseline(w, X, Q, sample_q, threads):
+def run_cpu_baseline(w, X, Q, sample_q, threads, alpha=None, beta=None):
     import oracle
-    T = oracle.collision_threshold(w.alpha, w.n)
-    C = oracle.candidate_count(w.beta, w.n, w.k)
+    alpha = w.alpha if alpha is None else alpha
+    beta = w.beta if beta is None else beta
+    T = oracle.collision_threshold(alpha, w.n)
+    C = oracle.candidate_count(beta, w.n, w.k)
     from paper_2411_14754_gb300 import workloads as W
     t0 = time.time()
     idx = oracle.build_index(X, w.Ns, w.sqrtK, 2, W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK),
@@ -150,7 +162,8 @@ def run_cpu_baseline(w, X, Q, sample_q, threads):
     oracle.query_batch(X, idx, Q[:sample_q], w.k, T, C, rank_precision=0, nthreads=threads)
     dt = time.time() - t0
     return {"value": sample_q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{sample_q} queries of the same workload, FP64 oracle (Algorithms 3-4), OpenMP over queries "
+            "sample": f"{sample_q} queries of the same workload at alpha={alpha}, beta={beta}, FP64 oracle "
+                      f"(Algorithms 3-4), OpenMP over queries "
                       f"on {threads} host threads; oracle index built with 2 Lloyd iterations in {build_s:.1f}s "
                       f"(index build not timed)", "seconds": dt}
 
@@ -189,6 +202,219 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# fixed (alpha, beta) points the plain arm may take; its operating point is the
+# fastest one whose mean recall reaches the target on the evaluation queries
+PLAIN_ALPHAS = (0.02, 0.05, 0.08, 0.12, 0.16, 0.2, 0.25, 0.3, 0.4)
+PLAIN_BETAS = (0.002, 0.005, 0.008, 0.012, 0.016, 0.024, 0.032)
+
+
+def time_loop(torch, stream, steps, warmup, fn, marks=1):
+    """Runs fn(s, ev) for warmup + steps steps; a timed step may record its
+    internal marks ev[0 .. marks-2]; the step's start and end are recorded
+    here.  Returns (total ms, per-step ms of each of the ``marks`` parts),
+    measured with CUDA events on ``stream``."""
+    for s in range(warmup):
+        fn(s, None)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(marks + 1)] for _ in range(steps)]
+    for s in range(steps):
+        ev[s][0].record(stream)
+        fn(warmup + s, ev[s][1:marks])
+        ev[s][marks].record(stream)
+    torch.cuda.synchronize()
+    total = ev[0][0].elapsed_time(ev[-1][-1])
+    parts = [[ev[s][j].elapsed_time(ev[s][j + 1]) for j in range(marks)] for s in range(steps)]
+    return total, parts
+
+
+def note(msg, t0=[time.time()]):  # noqa: B006 (start time of the process)
+    print(f"[bench {time.time() - t0[0]:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
+def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
+    """Learned per-query ratios vs plain fixed ratios, each at its fastest
+    operating point with mean recall@k >= target on the evaluation queries."""
+    from paper_2411_14754_gb300 import learn as L
+    w = W.WORKLOADS[args.workload]
+    t_setup = time.time()
+    X = W.dataset(w.number)
+    Xd = torch.from_numpy(X).to(dev)
+    t0 = time.time()
+    index = pkg.suco_build_index(Xd, w.Ns, w.sqrtK, w.kmeans_iters,
+                                 init_ids=W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK))
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    note(f"index built in {build_s:.1f}s")
+    # the network is trained on this GPU (setup, not timed)
+    n_train = args.n_train or w.n_train
+    t0 = time.time()
+    Qt = torch.from_numpy(W.queries(w.number, nq=n_train, train=True)).to(dev)
+    model, rep = L.fit(index, Xd, Qt, w.k, target=args.target_recall, log=note)
+    del Qt
+    train_s = time.time() - t0
+    note(f"trained: {json.dumps(rep)}")
+    Qall = W.queries(w.number)
+    Qe = torch.from_numpy(Qall).to(dev)
+    gt = L.exact_knn(Xd, Qe, w.k)
+    del Xd
+    target = args.target_recall
+    stream = torch.cuda.current_stream(dev)
+
+    # learned operating point: the smallest margin reaching the target
+    margin, rec_learned = L.tune_offsets(index, model, Qe, gt, w.k, target=target)
+    model.offsets = (margin, margin)
+    note(f"learned operating point: margin {margin}, recall {rec_learned:.4f}")
+    B = w.batch
+    nb = (w.nq + B - 1) // B
+    batches = [Qe[i * B:(i + 1) * B] for i in range(nb)]
+    order = [(rank + i * world) % nb for i in range(nb)]
+    outs = [(torch.empty((b.shape[0], w.k), dtype=torch.int32, device=dev),
+             torch.empty((b.shape[0], w.k), dtype=torch.float32, device=dev)) for b in batches]
+    ab = [(torch.empty(b.shape[0], device=dev), torch.empty(b.shape[0], device=dev)) for b in batches]
+    st = model.struct()
+
+    def learned_step(s, ev, q=None):
+        bi = order[s % nb]
+        qb = batches[bi] if q is None else q
+        pkg.suco_mlp_predict(index, st, qb, alpha=ab[bi][0], beta=ab[bi][1], stream=stream)
+        if ev:
+            ev[0].record(stream)
+        pkg.suco_query_batch(index, qb, w.k, L.FALLBACK[0], L.BETA_RANGE[1], out_ids=outs[bi][0],
+                             out_dist=outs[bi][1], alpha_per_query=ab[bi][0], beta_per_query=ab[bi][1], stream=stream)
+        return qb.shape[0]
+
+    def plain_step_fn(alpha, beta):
+        def f(s, ev):
+            bi = order[s % nb]
+            pkg.suco_query_batch(index, batches[bi], w.k, alpha, beta, out_ids=outs[bi][0], out_dist=outs[bi][1],
+                                 stream=stream)
+        return f
+
+    # plain operating point: fastest grid point whose recall reaches the target
+    plain = None
+    rec_grid = {}
+    for a in PLAIN_ALPHAS:
+        for bt in PLAIN_BETAS:
+            ids, _ = pkg.suco_query_batch(index, Qe, w.k, a, bt)
+            r = float(L.recall_rows(ids.cpu().numpy(), gt).mean())
+            rec_grid[f"{a},{bt}"] = r
+            if r >= target:
+                ms, _ = time_loop(torch, stream, 2 * nb, 2, plain_step_fn(a, bt))
+                qps = 2 * w.nq / (ms / 1000.0)
+                if plain is None or qps > plain["qps_probe"]:
+                    plain = {"alpha": a, "beta": bt, "recall_at_k": r, "qps_probe": qps}
+    note(f"plain operating point: {plain}")
+    setup_s = time.time() - t_setup
+
+    # timed region: the learned path, one predict + one query launch per batch
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    nq_step = [batches[order[s % nb]].shape[0] for s in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        total_ms, parts = time_loop(torch, stream, args.steps, args.warmup, learned_step, marks=2)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    nqueries = float(sum(nq_step))
+    tot = torch.tensor([total_ms, nqueries], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx, sm = tot.clone(), tot.clone()
+        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
+        total_ms, all_q = float(mx[0]), float(sm[1])
+    else:
+        all_q = nqueries
+    value = all_q / (total_ms / 1000.0)
+    predict_ms = statistics.mean(p[0] for p in parts)
+    query_ms = statistics.mean(p[1] for p in parts)
+
+    # the plain arm timed the same way (for the comparison)
+    plain_line = None
+    if plain is not None:
+        pms, _ = time_loop(torch, stream, args.steps, args.warmup, plain_step_fn(plain["alpha"], plain["beta"]))
+        plain_line = dict(plain, value=sum(nq_step) / (pms / 1000.0), unit=UNIT, ms_per_step=pms / args.steps)
+        plain_line.pop("qps_probe")
+
+    # end to end through the public API: pinned host queries in, host results out
+    hq = [b.cpu().pin_memory() for b in batches]
+    hout = [(torch.empty(o[0].shape, dtype=torch.int32).pin_memory(),
+             torch.empty(o[1].shape, dtype=torch.float32).pin_memory()) for o in outs]
+    dq = [torch.empty_like(b) for b in batches]
+    h2d = d2h = 0
+
+    def e2e_step(s, ev):
+        bi = order[s % nb]
+        dq[bi].copy_(hq[bi], non_blocking=True)
+        learned_step(s, None, q=dq[bi])
+        hout[bi][0].copy_(outs[bi][0], non_blocking=True)
+        hout[bi][1].copy_(outs[bi][1], non_blocking=True)
+
+    e2e_ms, _ = time_loop(torch, stream, args.steps, args.warmup, e2e_step)
+    for s in range(args.steps):
+        bi = order[(args.warmup + s) % nb]
+        h2d += hq[bi].numel() * 4
+        d2h += hout[bi][0].numel() * 4 + hout[bi][1].numel() * 4
+    e2e_value = sum(nq_step) / (e2e_ms / 1000.0)
+    if world > 1:
+        t = torch.tensor([e2e_ms, float(sum(nq_step))], dtype=torch.float64, device=dev)
+        mx, sm = t.clone(), t.clone()
+        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
+        e2e_value = float(sm[1]) / (float(mx[0]) / 1000.0)
+
+    # roofline of the query kernel: per query 4 * sum_i T_eff,i id bytes and
+    # 4 * C_b * d row bytes, C_b from the query's own beta
+    bytes_steps = 0.0
+    per_batch = {}
+    for bi in set(order[(args.warmup + s) % nb] for s in range(args.steps)):
+        al, be = L.predict(index, model, batches[bi])
+        dbg = pkg.suco_query_debug(index, batches[bi], w.k, L.FALLBACK[0], L.BETA_RANGE[1], want=("t_eff",),
+                                   alpha_per_query=al, beta_per_query=be)
+        teff = float(dbg["t_eff"].double().sum().item())
+        Cs = sum(pkg.suco_thresholds(w.n, L.FALLBACK[0], min(float(x), L.BETA_RANGE[1]), w.k)[1]
+                 for x in be.cpu().numpy())
+        per_batch[bi] = 4.0 * teff + 4.0 * Cs * w.d
+    for s in range(args.steps):
+        bytes_steps += per_batch[order[(args.warmup + s) % nb]]
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    achieved = bytes_steps / args.steps / (query_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": committed_traffic(w.number), "peak_source": peak_src,
+                "kernel": "suco_query_kernel (learned per-query alpha/beta, one launch per batch)",
+                "algorithmic_bytes_per_query": bytes_steps / sum(nq_step), "mean_launch_ms": query_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as _o
+        pa, pb = (plain["alpha"], plain["beta"]) if plain else (w.alpha, w.beta)
+        cpu = run_cpu_baseline(w, X, Qall, 32, _o.max_threads(), alpha=pa, beta=pb)
+
+    if rank == 0:
+        cfg = workload_config(w, B)
+        cfg["workload"] = (f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, k={w.k}, learned per-query "
+                           f"alpha/beta (MLP {3 * w.Ns}-{model.H}-2, GELU, BF16 weights), FP32 distances")
+        cfg["n_train"] = n_train
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": cfg, "recall_at_k": rec_learned, "k": w.k, "target_recall": target,
+                "margin": margin, "plain_fp32": plain_line,
+                "speedup_vs_plain": (value / plain_line["value"]) if plain_line else None,
+                "predict_ms_per_step": predict_ms, "query_ms_per_step": query_ms,
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                        "d2h_bytes_per_step": d2h // args.steps},
+                "clocks": clk.summary(), "gpu_launches": 2 * args.steps,
+                "index_build_s": build_s, "train_s": train_s, "setup_s": setup_s,
+                "training": rep, "plain_grid_recall": rec_grid}
+        print(json.dumps(line), flush=True)
+    pkg.suco_free(index)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -207,6 +433,11 @@ def main():
     dev = torch.device("cuda", local_rank)
     pkg.load_library()
     w = W.WORKLOADS[args.workload]
+    if w.n_train:
+        run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev)
+        if world > 1:
+            tdist.destroy_process_group()
+        return
     X = W.dataset(w.number)
     Qall = W.queries(w.number)
     Xd = torch.from_numpy(X).to(dev)

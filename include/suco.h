@@ -158,6 +158,61 @@ SUCO_API int suco_query_debug(const suco_index* index, const float* queries, int
 SUCO_API int suco_autotune(suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
                            void* stream, int32_t* cluster_size, int32_t* threads);
 
+/* ---- Learned per-query ratios (no counterpart in the paper, whose conclusion
+ * names learning as future work).  A small MLP maps per-query features to
+ * (log alpha, log beta); the query path then takes them as alpha_per_query and
+ * beta_per_query.
+ * Features (3*Ns per query, in this order): for each subspace i the smallest
+ * squared distance to a first-half centroid and to a second-half centroid
+ * (FP32, same arithmetic as the query's cell ranking), at index 2i and 2i+1;
+ * then log(1 + size of the cell of those two nearest centroids) at 2Ns+i.
+ * Network: xn = (x - mean) / std; z1 = xn W1 + b1; h = GELU(z1) (erf form);
+ * y = h W2 + b2.  W1 [in_dim][hidden] and W2 [hidden][2] are BF16 (raw 16-bit
+ * patterns), everything else FP32; every sum is FP32. */
+typedef struct suco_mlp {
+    int32_t in_dim;          /* 3*Ns for predict; 1..1024 for forward and backward  */
+    int32_t hidden;          /* 1..4096                                             */
+    int32_t out_dim;         /* must be 2                                           */
+    int32_t reserved0;       /* must be 0                                           */
+    const uint16_t* w1;      /* (device) [in_dim][hidden] BF16                      */
+    const float* b1;         /* (device) [hidden]                                   */
+    const uint16_t* w2;      /* (device) [hidden][2] BF16                           */
+    const float* b2;         /* (device) [2]                                        */
+    const float* feat_mean;  /* (device) [in_dim]                                   */
+    const float* feat_std;   /* (device) [in_dim], nonzero                           */
+    float out_offset[2];     /* margins added to y before use                       */
+    float log_alpha_min, log_alpha_max, log_beta_min, log_beta_max;  /* clamps      */
+    float fallback_alpha, fallback_beta;  /* used when an output is not finite      */
+} suco_mlp;
+
+/* Features of nq queries into feats (device, [nq][3*Ns]). */
+SUCO_API int suco_query_features(const suco_index* index, const float* queries, int64_t nq, float* feats,
+                                 void* stream);
+
+/* Features, network and ratios in one launch: alpha[b] = exp(clamp(y0 + off0)),
+ * beta[b] = exp(clamp(y1 + off1)) (device [nq] each), or the fallback ratios
+ * when an output is not finite. */
+SUCO_API int suco_mlp_predict(const suco_index* index, const suco_mlp* model, const float* queries, int64_t nq,
+                              float* alpha, float* beta, void* stream);
+
+/* Training pieces (device buffers; B samples of x [B][in_dim]):
+ * forward writes z1, h ([B][hidden], nullable) and y [B][2]; backward takes
+ * target [B][2], loss = mean over samples and outputs of (y - target)^2, and
+ * writes dz1 [B][hidden] and dy [B][2] (workspace), the gradients dw1, db1,
+ * dw2, db2 (FP32, same shapes as the weights; sums over samples are taken in
+ * sample order) and *loss.  AdamW updates FP32 master values in place (step
+ * counts from 1) and, if bf16_copy is given, writes their BF16 rounding.
+ * Errors: SUCO_EINVAL for a NULL buffer, B < 1 (backward) or model sizes out
+ * of range; the loss buffer is cleared by backward itself. */
+SUCO_API int suco_mlp_forward(const suco_mlp* model, const float* x, int64_t B, float* z1, float* h, float* y,
+                              void* stream);
+SUCO_API int suco_mlp_backward(const suco_mlp* model, const float* x, int64_t B, const float* z1, const float* h,
+                               const float* y, const float* target, float* dz1, float* dy, float* dw1, float* db1,
+                               float* dw2, float* db2, float* loss, void* stream);
+SUCO_API int suco_adamw_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr,
+                             float beta1, float beta2, float eps, float weight_decay, int32_t step, uint16_t* bf16_copy,
+                             void* stream);
+
 /* Sizes of an index. */
 typedef struct suco_index_info {
     int64_t n;

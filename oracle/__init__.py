@@ -5,3 +5,4 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 path (``paper_2411_14754_gb300``) never does; it shares no code with it.
 """
 from .suco_oracle import *  # noqa: F401,F403
+from . import mlp_oracle  # noqa: F401,E402

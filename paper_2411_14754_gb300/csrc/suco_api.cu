@@ -68,6 +68,8 @@ void free_index_memory(DeviceIndex* ix)
     cudaFree(ix->cell_off);
     cudaFree(ix->perm);
     cudaFree(ix->split);
+    cudaFree(ix->work);
+    ix->work = nullptr;
     ix->X = nullptr;
     ix->cent = nullptr;
     ix->cell_off = nullptr;
@@ -112,6 +114,7 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
         {(void**)&ix->cell_off, (size_t)Ns * (ix->K + 1) * 4},
         {(void**)&ix->perm, (size_t)Ns * n * 4},
         {(void**)&ix->split, (size_t)Ns * (NCH + 1) * ix->K * 4},
+        {(void**)&ix->work, (size_t)WORK_SLOTS * WORK_STRIDE * 4},
     };
     ix->bytes = 0;
     for (auto& e : a) {
@@ -124,6 +127,7 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
         ix->bytes += (int64_t)e.b;
     }
     SUCO_CUDA_TRY(cudaMemsetAsync(ix->cent, 0, a[1].b, st));
+    SUCO_CUDA_TRY(cudaMemsetAsync(ix->work, 0, a[5].b, st));
     if (ix->ld != d) SUCO_CUDA_TRY(cudaMemsetAsync(ix->X, 0, a[0].b, st));
     SUCO_CUDA_TRY(cudaMemcpy2DAsync(ix->X, (size_t)ix->ld * 4, data, (size_t)d * 4, (size_t)d * 4, (size_t)n,
                                     cudaMemcpyDeviceToDevice, st));

@@ -15,6 +15,8 @@ namespace suco {
 // multiple of 32).  For every (subspace, cell) the index stores where each
 // chunk starts inside the cell's id list, so that a CTA that owns a chunk
 // range reads only its own ids of a cell.
+constexpr int WORK_SLOTS = 64;
+constexpr int WORK_STRIDE = 8;  // 32 bytes per slot
 constexpr int NCH = 16;
 
 struct DeviceIndex {
@@ -32,6 +34,12 @@ struct DeviceIndex {
     uint32_t* cell_off = nullptr; // [Ns][K+1] offsets into perm[i]
     int32_t* perm = nullptr;      // [Ns][n] ids grouped by cell, ascending inside a cell
     uint32_t* split = nullptr;    // [Ns][NCH+1][K] absolute position in perm[i] where chunk j starts in cell x
+    // work counters of persistent query launches: WORK_SLOTS pairs (next query,
+    // finished clusters), WORK_STRIDE words apart, zero between launches; calls
+    // take the slots in turn (work_next), so up to WORK_SLOTS calls on one index
+    // may be in flight at once
+    uint32_t* work = nullptr;
+    uint32_t work_next = 0;
     int device = 0;
     int64_t bytes = 0;
     // launch shapes chosen by suco_autotune, per (k, candidate bound C)

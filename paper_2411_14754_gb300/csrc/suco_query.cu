@@ -76,6 +76,7 @@ struct QArgs {
     const int32_t* k_per;    // optional per-query k, alpha, beta
     const float* alpha_per;
     const float* beta_per;
+    uint32_t* work;          // (next query, finished clusters) of this launch, zero at start; or null
     uint32_t span, G;  // ids per CTA, 32-id groups per CTA
     uint32_t nbits;    // B: bit planes of the sliced SC-score counts
     int32_t* out_ids;
@@ -700,9 +701,16 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     constexpr int NC = NSMAX + 2;  // count slots: [0] = valid ids, [s] = #scores >= s
     const uint32_t r = cluster_rank();
     const int CL = A.CL;
-    // persistent clusters: cluster c answers queries c, c + G, c + 2G, ... (G clusters in the grid)
-    for (int64_t b = blockIdx.x / CL; b < A.nq; b += gridDim.x / CL) {
+    // persistent clusters: cluster c starts with query c of the G clusters in the
+    // grid; with a work counter each cluster then takes the next unanswered query
+    // (queries of uneven cost balance), without one it answers c + G, c + 2G, ...
+    const uint32_t Gc = gridDim.x / (uint32_t)CL;
+    uint32_t* next_q = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 120;  // this cluster's next query
+    int64_t b = blockIdx.x / CL;
+    while (b < A.nq) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t grabbed = 0u;  // thread 0 of CTA 0: the query this cluster answers next
+    if (A.work && r == 0 && threadIdx.x == 0) grabbed = Gc + atomicAdd(A.work, 1u);
 
     // ---- S0: this query's thresholds; stage the query; clear the published
     // counts and candidate slots
@@ -753,6 +761,9 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         for (uint32_t w = threadIdx.x; w < n16; w += NT) pw[w] = z;
     }
     cluster_sync();  // #1: every subspace's cut and staircase are published
+    // every CTA has read the previous next_q before #1: publish the next query
+    if (A.work && r == 0 && threadIdx.x == 0)
+        for (int t = 0; t < CL; ++t) st_cluster_u32(map_rank(smem_addr(next_q), (uint32_t)t), grabbed);
 
     // ---- copy the other CTAs' tables
     {
@@ -1160,7 +1171,21 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
             A.out_dist[b * kst + t] = __int_as_float(0x7f800000);
         }
     }
-    }  // next query: the cluster barriers of its stages order every remote access
+    // next query: the cluster barriers of its stages order every remote access
+    // (next_q was written before #2 and is read after #4)
+    if (A.work) {
+        b = (int64_t)*reinterpret_cast<volatile uint32_t*>(next_q);
+    } else {
+        b += Gc;
+    }
+    }
+    // the last cluster to finish returns the work counter to zero for the next launch
+    if (A.work && r == 0 && threadIdx.x == 0) {
+        if (atomicAdd(A.work + 1, 1u) == Gc - 1u) {
+            atomicExch(A.work, 0u);
+            atomicExch(A.work + 1, 0u);
+        }
+    }
 }
 
 uint32_t align16(uint64_t x) { return (uint32_t)((x + 15) & ~uint64_t(15)); }
@@ -1207,8 +1232,6 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, in
     A.o_slots = (uint32_t)o;
     o = align16(o + 4ull * A.per_cta);
     A.sortP = next_pow2(std::max<uint32_t>(A.per_cta, 1));
-    A.o_keys = (uint32_t)o;
-    o = align16(o + 8ull * A.sortP);
     A.o_union = (uint32_t)o;
     A.nbits = nsmax == 8 ? 4 : (nsmax == 16 ? 5 : 6);
     const uint64_t plane_bytes = 4ull * A.nbits * A.G;
@@ -1216,9 +1239,13 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, in
     A.stage_cent = cent_bytes <= 65536 ? 1u : 0u;
     const uint64_t s3_bytes = S3_BYTES + (A.stage_cent ? cent_bytes : 0);
     const uint64_t row_bytes = 4ull * ix->ld;
-    const uint64_t s6_bytes = std::max<uint64_t>(4ull * NB + 8ull * SURV_CAP, 2 * 8 * row_bytes);
-    const uint64_t ubytes = std::max(plane_bytes, std::max(s3_bytes, s6_bytes));
-    A.rows_half = (uint32_t)std::max<uint64_t>(1, ubytes / 2 / row_bytes);
+    // S6 reuses the union: the row double buffer (or, after it, the distance
+    // histogram and survivors) at its start, the CTA's re-rank keys at its end
+    const uint64_t keys_bytes = align16(8ull * A.sortP);
+    const uint64_t s6_bytes = std::max<uint64_t>(4ull * NB + 8ull * SURV_CAP, 2 * 8 * row_bytes) + keys_bytes;
+    const uint64_t ubytes = align16(std::max(plane_bytes, std::max(s3_bytes, s6_bytes)));
+    A.o_keys = (uint32_t)(o + ubytes - keys_bytes);
+    A.rows_half = (uint32_t)std::max<uint64_t>(1, (ubytes - keys_bytes) / 2 / row_bytes);
     o = align16(o + ubytes);
     L->smem = o;
     return SUCO_OK;
@@ -1235,7 +1262,7 @@ std::mutex g_occ_mu;
 std::vector<std::pair<OccKey, int>> g_occ;
 
 template <int NT, int NSMAX>
-int launch_t(const Layout& L, int64_t nq, bool persistent, cudaStream_t st)
+int launch_t(const Layout& L, int64_t nq, bool persistent, uint32_t* work, cudaStream_t st)
 {
     auto kern = suco_query_kernel<NT, NSMAX>;
     SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
@@ -1253,6 +1280,8 @@ int launch_t(const Layout& L, int64_t nq, bool persistent, cudaStream_t st)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int64_t G = nq;
+    QArgs A = L.A;
+    A.work = nullptr;
     if (persistent) {
         int nclusters = 0;
         {
@@ -1272,9 +1301,10 @@ int launch_t(const Layout& L, int64_t nq, bool persistent, cudaStream_t st)
             }
         }
         if (nclusters > 0) G = std::min<int64_t>(nq, nclusters);
+        if (G < nq) A.work = work;
     }
     cfg.gridDim = dim3((unsigned)(G * L.A.CL), 1, 1);
-    SUCO_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, L.A));
+    SUCO_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, A));
     return SUCO_OK;
 }
 
@@ -1364,14 +1394,18 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
         A.dbg_cands = dbg->cands;
     }
     const bool persistent = (p->flags & SUCO_QUERY_ONE_CLUSTER_PER_QUERY) == 0;
+    // each call takes the next of the index's work counters in turn
+    uint32_t* work = ix->work + (size_t)WORK_STRIDE *
+                                    (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next, 1u,
+                                                        __ATOMIC_RELAXED) % WORK_SLOTS);
     if (NT == 1024) {
-        if (nsmax == 8) return launch_t<1024, 8>(L, nq, persistent, st);
-        if (nsmax == 16) return launch_t<1024, 16>(L, nq, persistent, st);
-        return launch_t<1024, 32>(L, nq, persistent, st);
+        if (nsmax == 8) return launch_t<1024, 8>(L, nq, persistent, work, st);
+        if (nsmax == 16) return launch_t<1024, 16>(L, nq, persistent, work, st);
+        return launch_t<1024, 32>(L, nq, persistent, work, st);
     }
-    if (nsmax == 8) return launch_t<512, 8>(L, nq, persistent, st);
-    if (nsmax == 16) return launch_t<512, 16>(L, nq, persistent, st);
-    return launch_t<512, 32>(L, nq, persistent, st);
+    if (nsmax == 8) return launch_t<512, 8>(L, nq, persistent, work, st);
+    if (nsmax == 16) return launch_t<512, 16>(L, nq, persistent, work, st);
+    return launch_t<512, 32>(L, nq, persistent, work, st);
 }
 
 }  // namespace suco

@@ -38,6 +38,15 @@ class _DebugOut(C.Structure):
                 ("cands", C.c_void_p)]
 
 
+class SucoMlp(C.Structure):
+    """ctypes mirror of suco_mlp (device pointers as integers)."""
+    _fields_ = [("in_dim", C.c_int32), ("hidden", C.c_int32), ("out_dim", C.c_int32), ("reserved0", C.c_int32),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("feat_mean", C.c_void_p), ("feat_std", C.c_void_p), ("out_offset", C.c_float * 2),
+                ("log_alpha_min", C.c_float), ("log_alpha_max", C.c_float), ("log_beta_min", C.c_float),
+                ("log_beta_max", C.c_float), ("fallback_alpha", C.c_float), ("fallback_beta", C.c_float)]
+
+
 class _IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("Ns", C.c_int32), ("sqrtK", C.c_int32), ("hmax", C.c_int32),
                 ("K", C.c_int64), ("ld", C.c_int64), ("device_bytes", C.c_int64)]
@@ -67,12 +76,19 @@ def load_library():
     L.suco_thresholds.argtypes = [i64, f64, f64, i32, C.POINTER(i64), C.POINTER(i64)]
     L.suco_kmeans_noalloc.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, vp]
     L.suco_autotune.argtypes = [vp, vp, i64, C.POINTER(_QueryParams), vp, C.POINTER(i32), C.POINTER(i32)]
+    L.suco_query_features.argtypes = [vp, vp, i64, vp, vp]
+    L.suco_mlp_predict.argtypes = [vp, C.POINTER(SucoMlp), vp, i64, vp, vp, vp]
+    L.suco_mlp_forward.argtypes = [C.POINTER(SucoMlp), vp, i64, vp, vp, vp, vp]
+    L.suco_mlp_backward.argtypes = [C.POINTER(SucoMlp), vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.suco_adamw_step.argtypes = [vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
+                                  i32, vp, vp]
     L.suco_free.argtypes = [vp]
     L.suco_free.restype = None
     L.suco_last_error.restype = C.c_char_p
     for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_query_batch", "suco_query_debug",
                  "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version",
-                 "suco_kmeans_noalloc", "suco_autotune"):
+                 "suco_kmeans_noalloc", "suco_autotune", "suco_query_features", "suco_mlp_predict",
+                 "suco_mlp_forward", "suco_mlp_backward", "suco_adamw_step"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -219,6 +235,51 @@ def suco_autotune(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float,
     _check(load_library().suco_autotune(index.handle, _ptr(queries), nq, C.byref(p), _stream(stream), C.byref(cl),
                                         C.byref(nt)))
     return cl.value, nt.value
+
+
+def suco_query_features(index: SucoIndex, queries: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None):
+    """Per-query features [nq][3*Ns] (see include/suco.h)."""
+    _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    if out is None:
+        out = torch.empty((nq, 3 * index.Ns), dtype=torch.float32, device=queries.device)
+    _check(load_library().suco_query_features(index.handle, _ptr(queries), nq, _ptr(out), _stream(stream)))
+    return out
+
+
+def suco_mlp_predict(index: SucoIndex, model: SucoMlp, queries: torch.Tensor, alpha: Optional[torch.Tensor] = None,
+                     beta: Optional[torch.Tensor] = None, stream=None):
+    """Per-query (alpha, beta) float32 CUDA tensors from the network."""
+    _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    if alpha is None:
+        alpha = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    if beta is None:
+        beta = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    _check(load_library().suco_mlp_predict(index.handle, C.byref(model), _ptr(queries), nq, _ptr(alpha), _ptr(beta),
+                                           _stream(stream)))
+    return alpha, beta
+
+
+def suco_mlp_forward(model: SucoMlp, x: torch.Tensor, z1=None, h=None, y=None, stream=None):
+    _dev_f32(x, "x")
+    B = x.shape[0]
+    if y is None:
+        y = torch.empty((B, 2), dtype=torch.float32, device=x.device)
+    _check(load_library().suco_mlp_forward(C.byref(model), _ptr(x), B, _ptr(z1), _ptr(h), _ptr(y), _stream(stream)))
+    return y
+
+
+def suco_mlp_backward(model: SucoMlp, x, z1, h, y, target, dz1, dy, dw1, db1, dw2, db2, loss, stream=None):
+    _check(load_library().suco_mlp_backward(C.byref(model), _ptr(x), x.shape[0], _ptr(z1), _ptr(h), _ptr(y),
+                                            _ptr(target), _ptr(dz1), _ptr(dy), _ptr(dw1), _ptr(db1), _ptr(dw2),
+                                            _ptr(db2), _ptr(loss), _stream(stream)))
+
+
+def suco_adamw_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,
+                    bf16_copy=None, stream=None):
+    _check(load_library().suco_adamw_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2,
+                                          eps, weight_decay, int(step), _ptr(bf16_copy), _stream(stream)))
 
 
 def suco_index_get_info(index: SucoIndex) -> dict:

@@ -292,3 +292,41 @@ def test_query_replays_from_a_cuda_graph(tiny):
     torch.cuda.synchronize()
     assert torch.equal(ids, ref2[0])
     pkg.suco_free(ix)
+
+
+def test_work_counter_answers_every_query_once_across_calls_and_replays(tiny):
+    # many more queries than resident clusters, of very uneven cost: the
+    # persistent launch hands queries out through the index's work counters,
+    # which must cover every query once per call and be back at zero for the
+    # next call (plain calls, calls on a second stream, graph replays)
+    w, X, Q, idx = tiny
+    dev = torch.device("cuda")
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).to(dev), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    nq = 3000
+    Qd = torch.from_numpy(W.queries(1, nq=nq)).to(dev)
+    rng = np.random.default_rng(5)
+    al = torch.from_numpy(rng.choice([0.005, 0.05, 0.6], nq, p=[0.6, 0.3, 0.1]).astype(np.float32)).to(dev)
+    kw = dict(alpha_per_query=al)
+    ref = pkg.suco_query_batch(ix, Qd, w.k, 0.05, w.beta, flags=pkg.suco.QUERY_ONE_CLUSTER_PER_QUERY, **kw)
+    for _ in range(3):
+        got = pkg.suco_query_batch(ix, Qd, w.k, 0.05, w.beta, **kw)
+        torch.cuda.synchronize()
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    ids = torch.empty((nq, w.k), dtype=torch.int32, device=dev)
+    dist = torch.empty((nq, w.k), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(s):
+        pkg.suco_query_batch(ix, Qd, w.k, 0.05, w.beta, out_ids=ids, out_dist=dist, stream=s, **kw)
+    s.synchronize()
+    assert torch.equal(ids, ref[0])
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pkg.suco_query_batch(ix, Qd, w.k, 0.05, w.beta, out_ids=ids, out_dist=dist, stream=s, **kw)
+    for _ in range(3):
+        ids.fill_(-7)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(ids, ref[0]) and torch.equal(dist, ref[1])
+    pkg.suco_free(ix)
