@@ -55,6 +55,7 @@ constexpr int SCAN_U = 8;     // ids in flight per lane in the scan
 
 constexpr int S3_BYTES = 4 * NB + 12 * MCAP;  // S3 scratch at the start of the union region
 constexpr int SURV_CAP = 512; // keys kept for the final sort of a local top-k
+constexpr int S6_CH = 4;      // float4 chunks per lane per row in one S6 load round
 
 struct QArgs {
     const float* __restrict__ X;
@@ -79,6 +80,7 @@ struct QArgs {
     uint32_t* work;          // (next query, finished clusters) of this launch, zero at start; or null
     uint32_t span, G;  // ids per CTA, 32-id groups per CTA
     uint32_t nbits;    // B: bit planes of the sliced SC-score counts
+    uint32_t nsets, nplanes, nstore;  // S4 counters: 4-bit nibble sets, one-bit planes, words per 32 ids
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -90,7 +92,6 @@ struct QArgs {
     uint32_t o_tab, tab_stride, o_q, o_hist, o_misc, o_cnt, o_seg, o_slots, o_keys, o_union;
     uint32_t sortP;       // power of two >= the CTA's candidate share (fallback sort)
     uint32_t stage_cent;  // 1: the subspace's centroids are staged in shared memory
-    uint32_t rows_half;   // candidate rows per half of the S6 double buffer
 };
 
 // ---------------------------------------------------------------------------
@@ -132,20 +133,14 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v)
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-// 16-byte asynchronous global -> shared copy (cached in L2 only), and its groups
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
+// 16-byte global load that bypasses L1 (candidate rows are read once)
+__device__ __forceinline__ float4 ldg_stream(const float4* p)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)),
-                 "l"(__cvta_generic_to_global(gsrc))
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -578,22 +573,31 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
 
 // S4 for entries [e0, e0+m) of the flattened retrieved-cell list (all
 // subspaces, subspace-major): build the segments (this CTA's part of each
-// cell's id list), then increment the sliced counts of their ids.
-template <int NT, int B>
+// cell's id list), then count their ids.  An id occurs at most once per
+// subspace (every point lies in exactly one cell of each IMI), so subspace i
+// adds 1 to the id's 4-bit counter of nibble set i / 15 (at most 15 increments
+// each, no overflow), or sets the id's bit in a one-bit plane for the
+// subspaces past the nibble sets: one shared-memory atomicAdd per id.
+// Layout of a nibble set (4 words per 32-id group g): id 32g + t sits in word
+// (t & 3) of the set, nibble t >> 2, i.e. bits [t & 28, (t & 28) + 4).
+template <int NT>
 __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t m, const uint32_t* sub_pre,
-                              uint32_t* planes, uint32_t id0, int j0, int j1)
+                              const uint32_t* sub_wb, uint32_t* cnt_words, uint32_t id0, int j0, int j1)
 {
-    // per segment: perm index of its first id minus its flat start
-    uint32_t* seg_base = reinterpret_cast<uint32_t*>(smem + A.o_seg);
-    uint32_t* seg_pre = seg_base + MAXSEG;  // [MAXSEG+1]
+    // the non-empty segments in flat order: (perm index of the first id minus
+    // the flat start, counter word base | nibble flag), and their flat starts
+    uint2* seg_info = reinterpret_cast<uint2*>(smem + A.o_seg);   // [MAXSEG]
+    uint32_t* seg_pre = reinterpret_cast<uint32_t*>(seg_info + MAXSEG);  // [MAXSEG+1]
     uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
     const int sk = A.sqrtK;
     constexpr int EPT = MAXSEG / NT;
-    uint32_t len[EPT], s = 0;
+    uint32_t len[EPT], pbase[EPT], mode[EPT], s = 0, ne = 0;
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
         const uint32_t e = threadIdx.x * EPT + u;
         len[u] = 0;
+        pbase[u] = 0;
+        mode[u] = 0;
         if (e < m) {
             const uint32_t g = e0 + e;
             int i = 0;
@@ -611,66 +615,134 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
             const uint32_t s0 = __ldg(sp + (int64_t)j0 * A.K);
             const uint32_t s1 = __ldg(sp + (int64_t)j1 * A.K);
             len[u] = s1 - s0;
-            seg_base[e] = (uint32_t)i * (uint32_t)A.n + s0;
+            pbase[u] = (uint32_t)i * (uint32_t)A.n + s0;
+            mode[u] = sub_wb[i];
         }
         s += len[u];
+        ne += len[u] ? 1u : 0u;
     }
-    uint32_t F;
+    uint32_t F, M;
     uint32_t run = block_exclusive_scan<NT>(s, wtmp, &F);
+    uint32_t slot = block_exclusive_scan<NT>(ne, wtmp, &M);
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
-        const uint32_t e = threadIdx.x * EPT + u;
-        if (e < m) {
-            seg_pre[e] = run;
-            seg_base[e] -= run;  // perm index = base + flat position (mod 2^32)
+        if (len[u]) {
+            seg_pre[slot] = run;
+            seg_info[slot] = make_uint2(pbase[u] - run, mode[u]);  // perm index = .x + flat position (mod 2^32)
+            ++slot;
         }
         run += len[u];
     }
-    if (threadIdx.x == 0) seg_pre[m] = F;
+    if (threadIdx.x == 0) seg_pre[M] = F;
     __syncthreads();
-    // each warp takes a contiguous share of the F ids; lanes stride by 32
+    // each warp takes a contiguous share [wb, we) of the F ids in windows of 32
+    // consecutive positions (one per lane); the warp holds the starts of the
+    // next 32 segments in its lanes, so a lane finds the segment of its
+    // position with a ballot and a population count instead of a walk
     constexpr int NW = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t share = (F + NW - 1) / NW;
     const uint32_t wb = min(F, (uint32_t)warp * share), we = min(F, wb + share);
-    if (wb + lane < we) {
-        uint32_t p = wb + lane;
-        int lo = 0, hi = (int)m - 1;  // last segment starting at or before p
+    uint32_t lanemask_le;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(lanemask_le));
+    if (wb < we) {
+        int lo = 0, hi = (int)M - 1;  // the segment holding wb
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (seg_pre[mid] <= p) lo = mid; else hi = mid - 1;
+            if (seg_pre[mid] <= wb) lo = mid; else hi = mid - 1;
         }
-        int sg = lo;
-        const uint32_t span = A.span;
-        for (; p < we; p += 32 * SCAN_U) {
+        uint32_t sg0 = (uint32_t)lo;
+        const uint32_t span = A.span, G = A.G;
+        for (uint32_t w0 = wb; w0 < we;) {
+            const uint32_t sj = sg0 + 1u + (uint32_t)lane;
+            const uint32_t Bj = sj <= M ? seg_pre[sj] : 0xffffffffu;  // start of segment sg0+1+lane
+            const uint32_t B31 = __shfl_sync(0xffffffffu, Bj, 31);
+            const uint32_t wend = min(we, min(w0 + 32u * SCAN_U, B31));  // segments sg0 .. sg0+31 only
             int32_t idv[SCAN_U];
+            uint32_t md[SCAN_U];
 #pragma unroll
             for (int u = 0; u < SCAN_U; ++u) {
-                const uint32_t pu = p + 32 * u;
+                const uint32_t x = w0 + 32u * (uint32_t)u, pu = x + (uint32_t)lane;
+                const uint32_t before = __popc(__ballot_sync(0xffffffffu, Bj <= x));
+                const uint32_t o = Bj - x;  // segment starts strictly inside the window
+                const uint32_t mk = __reduce_or_sync(0xffffffffu, o - 1u < 31u ? 1u << o : 0u);
                 idv[u] = -1;
-                if (pu < we) {
-                    while (seg_pre[sg + 1] <= pu) ++sg;
-                    idv[u] = __ldg(A.perm + (uint32_t)(seg_base[sg] + pu));
+                md[u] = 0u;
+                if (pu < wend) {
+                    const uint2 inf = seg_info[sg0 + before + __popc(mk & lanemask_le)];
+                    md[u] = inf.y;
+                    idv[u] = __ldg(A.perm + (uint32_t)(inf.x + pu));
                 }
             }
-            uint32_t word[SCAN_U], carry[SCAN_U];
 #pragma unroll
             for (int u = 0; u < SCAN_U; ++u) {
                 const uint32_t loc = (uint32_t)idv[u] - id0;
-                const bool ok = idv[u] >= 0 && loc < span;
-                word[u] = ok ? loc >> 5 : 0u;
-                carry[u] = ok ? 1u << (loc & 31u) : 0u;
+                if (idv[u] >= 0 && loc < span) {
+                    const uint32_t t = loc & 31u;
+                    const bool nib = (md[u] >> 31) != 0u;
+                    const uint32_t w = (md[u] & 0x7fffffffu) + (nib ? (t & 3u) * G : 0u) + (loc >> 5);
+                    atomicAdd(&cnt_words[w], 1u << (nib ? (t & 28u) : t));
+                }
             }
-            // add 1: toggle level j; carry on while the old bit was set
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-#pragma unroll
-                for (int u = 0; u < SCAN_U; ++u)
-                    if (carry[u]) carry[u] &= atomicXor(&planes[(uint32_t)j * A.G + word[u]], carry[u]);
-            }
+            sg0 += __popc(__ballot_sync(0xffffffffu, Bj <= wend));
+            w0 = wend;
         }
     }
     __syncthreads();
+}
+
+// Turns the counters of every 32-id group of this CTA into B bit planes in
+// place: plane j (word j*G + g) holds bit j of each id's SC-score.  A nibble
+// set's four words are a 4 x 4 bit matrix per nibble position (word q, bit l)
+// that is transposed with two rounds of masked swaps; the sets and the one-bit
+// planes are then added with bit-sliced ripple adders.
+template <int NT, int B>
+__device__ void counters_to_planes(const QArgs& A, uint32_t* w, uint32_t ngroups)
+{
+    const uint32_t G = A.G;
+    const int nsets = (int)A.nsets, nplanes = (int)A.nplanes;
+    for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
+        uint32_t acc[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc[j] = 0u;
+        for (int st = 0; st < nsets; ++st) {
+            uint32_t x0 = w[(4 * st + 0) * G + g], x1 = w[(4 * st + 1) * G + g];
+            uint32_t x2 = w[(4 * st + 2) * G + g], x3 = w[(4 * st + 3) * G + g];
+            uint32_t t = ((x0 >> 2) ^ x2) & 0x33333333u;
+            x2 ^= t;
+            x0 ^= t << 2;
+            t = ((x1 >> 2) ^ x3) & 0x33333333u;
+            x3 ^= t;
+            x1 ^= t << 2;
+            t = ((x0 >> 1) ^ x1) & 0x55555555u;
+            x1 ^= t;
+            x0 ^= t << 1;
+            t = ((x2 >> 1) ^ x3) & 0x55555555u;
+            x3 ^= t;
+            x2 ^= t << 1;
+            // now x_l holds bit l of the set's count of id 32g + t at bit t
+            const uint32_t add[4] = {x0, x1, x2, x3};
+            uint32_t c = 0u;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const uint32_t y = j < 4 ? add[j] : 0u;
+                const uint32_t s = acc[j] ^ y ^ c;
+                c = (acc[j] & y) | (c & (acc[j] ^ y));
+                acc[j] = s;
+            }
+        }
+        for (int pl = 0; pl < nplanes; ++pl) {
+            uint32_t c = w[(4 * nsets + pl) * G + g];
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const uint32_t s = acc[j] ^ c;
+                c &= acc[j];
+                acc[j] = s;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) w[(uint32_t)j * G + g] = acc[j];
+    }
 }
 
 // The sliced SC-scores of 32-id group g: acc[j] holds bit j of each id's score.
@@ -707,6 +779,14 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     const uint32_t Gc = gridDim.x / (uint32_t)CL;
     uint32_t* next_q = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 120;  // this cluster's next query
     int64_t b = blockIdx.x / CL;
+    // where subspace i counts its collisions (word base | nibble-set flag)
+    uint32_t* sub_wb = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 128;  // [Ns]
+
+    for (int i = threadIdx.x; i < A.Ns; i += NT) {
+        const uint32_t ns15 = 15u * A.nsets;
+        sub_wb[i] = (uint32_t)i < ns15 ? (4u * ((uint32_t)i / 15u) * A.G) | 0x80000000u
+                                       : (4u * A.nsets + (uint32_t)i - ns15) * A.G;
+    }
     while (b < A.nq) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t grabbed = 0u;  // thread 0 of CTA 0: the query this cluster answers next
@@ -745,8 +825,6 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         for (int j = threadIdx.x; j < A.ld; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
         uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);
         for (int t = threadIdx.x; t < NC; t += NT) cnt[t] = 0u;
-        uint32_t* sl = reinterpret_cast<uint32_t*>(smem + A.o_slots);
-        for (uint32_t t = threadIdx.x; t < A.per_cta; t += NT) sl[t] = 0xffffffffu;
     }
     __syncthreads();
 
@@ -757,7 +835,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     {
         uint4* pw = reinterpret_cast<uint4*>(smem + A.o_union);
         const uint4 z = make_uint4(0, 0, 0, 0);
-        const uint32_t n16 = (B * A.G + 3) / 4;  // the union region is a multiple of 16 bytes
+        const uint32_t n16 = (A.nstore * A.G + 3) / 4;  // the union region is a multiple of 16 bytes
         for (uint32_t w = threadIdx.x; w < n16; w += NT) pw[w] = z;
     }
     cluster_sync();  // #1: every subspace's cut and staircase are published
@@ -791,12 +869,20 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         sub_pre[A.Ns] = acc;
     }
     __syncthreads();
-    uint32_t* planes = reinterpret_cast<uint32_t*>(smem + A.o_union);  // [B][G] sliced counts
+    uint32_t* planes = reinterpret_cast<uint32_t*>(smem + A.o_union);  // counters, then [B][G] sliced scores
     const uint32_t L = sub_pre[A.Ns];
     for (uint32_t e0 = 0; e0 < L; e0 += MAXSEG)
-        scan_segments<NT, B>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, planes, id0, j0, j1);
+        scan_segments<NT>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, sub_wb, planes, id0, j0, j1);
 
     const uint32_t valid = id0 >= A.n ? 0u : (uint32_t)min((int64_t)A.span, A.n - (int64_t)id0);
+    {
+        // the candidate slots share the (now dead) segment region; other CTAs
+        // fill them after cluster barrier #2
+        uint32_t* sl = reinterpret_cast<uint32_t*>(smem + A.o_slots);
+        for (uint32_t t = threadIdx.x; t < A.per_cta; t += NT) sl[t] = 0xffffffffu;
+    }
+    counters_to_planes<NT, B>(A, planes, (valid + 31) / 32);
+    __syncthreads();
     if (A.dbg_scores)
         for (uint32_t j = threadIdx.x; j < valid; j += NT) {
             uint32_t sc = 0;
@@ -949,54 +1035,67 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + A.o_keys);  // [sortP]
     const int ld4 = (int)(A.ld / 4);
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
-    float4* rowbuf = reinterpret_cast<float4*>(smem + A.o_union);  // two halves of rows_half rows
-    const uint32_t RH = A.rows_half;
-    // rows [r0, r0+RH) of the share go into half h with 16-byte asynchronous copies
-    auto issue = [&](uint32_t r0, uint32_t h) {
-        const uint32_t nr = min(RH, mine - r0);
-        float4* dst = rowbuf + (size_t)h * RH * ld4;
-        for (uint32_t rr = (uint32_t)warp; rr < nr; rr += NW) {
-            const uint32_t id = slots[r0 + rr];
-            if (id >= (uint32_t)A.n) continue;
-            const float4* src = reinterpret_cast<const float4*>(A.X + (int64_t)id * A.ld);
-            for (int c = lane; c < ld4; c += 32) cp_async16(dst + (size_t)rr * ld4 + c, src + c);
-        }
-        cp_async_commit();
-    };
-    if (mine > 0) issue(0, 0);
-    uint32_t half = 0;
-    for (uint32_t r0 = 0; r0 < mine; r0 += RH, half ^= 1u) {
-        if (r0 + RH < mine) {
-            issue(r0 + RH, half ^ 1u);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const uint32_t nr = min(RH, mine - r0);
-        const float4* src = rowbuf + (size_t)half * RH * ld4;
-        for (uint32_t rr = (uint32_t)warp; rr < nr; rr += NW) {
-            const uint32_t id = slots[r0 + rr];
-            float acc = 0.f;
-            for (int c = lane; c < ld4; c += 32) {
-                const float4 xv = src[(size_t)rr * ld4 + c];
-                const float4 qv = q4[c];
-                float df = __fsub_rn(xv.x, qv.x);
-                acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(xv.y, qv.y);
-                acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(xv.z, qv.z);
-                acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(xv.w, qv.w);
-                acc = __fmaf_rn(df, df, acc);
+    // 8 lanes per row, two groups of 4 rows per warp in flight; each lane keeps
+    // S6_CH float4 chunks of each of its two rows in registers per load round
+    {
+        const int grp = lane >> 3, gl = lane & 7;
+        const float4* X4 = reinterpret_cast<const float4*>(A.X);
+        for (uint32_t rb = (uint32_t)warp * 8u; rb < mine; rb += (uint32_t)NW * 8u) {
+            const uint32_t ra = rb + (uint32_t)grp, rc = ra + 4u;
+            const uint32_t ida = ra < mine ? slots[ra] : 0xffffffffu;
+            const uint32_t idc = rc < mine ? slots[rc] : 0xffffffffu;
+            const bool va = ida < (uint32_t)A.n, vc = idc < (uint32_t)A.n;
+            const float4* pa = X4 + (int64_t)(va ? ida : 0u) * ld4;
+            const float4* pc = X4 + (int64_t)(vc ? idc : 0u) * ld4;
+            float acc_a = 0.f, acc_c = 0.f;
+            for (int c0 = gl; c0 < ld4; c0 += 8 * S6_CH) {
+                float4 xa[S6_CH], xc[S6_CH];
+#pragma unroll
+                for (int u = 0; u < S6_CH; ++u) {
+                    const int c = c0 + 8 * u;
+                    xa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    xc[u] = xa[u];
+                    if (c < ld4) {
+                        if (va) xa[u] = ldg_stream(pa + c);
+                        if (vc) xc[u] = ldg_stream(pc + c);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < S6_CH; ++u) {
+                    const int c = c0 + 8 * u;
+                    if (c < ld4) {
+                        const float4 qv = q4[c];
+                        float df = __fsub_rn(xa[u].x, qv.x);
+                        acc_a = __fmaf_rn(df, df, acc_a);
+                        df = __fsub_rn(xa[u].y, qv.y);
+                        acc_a = __fmaf_rn(df, df, acc_a);
+                        df = __fsub_rn(xa[u].z, qv.z);
+                        acc_a = __fmaf_rn(df, df, acc_a);
+                        df = __fsub_rn(xa[u].w, qv.w);
+                        acc_a = __fmaf_rn(df, df, acc_a);
+                        df = __fsub_rn(xc[u].x, qv.x);
+                        acc_c = __fmaf_rn(df, df, acc_c);
+                        df = __fsub_rn(xc[u].y, qv.y);
+                        acc_c = __fmaf_rn(df, df, acc_c);
+                        df = __fsub_rn(xc[u].z, qv.z);
+                        acc_c = __fmaf_rn(df, df, acc_c);
+                        df = __fsub_rn(xc[u].w, qv.w);
+                        acc_c = __fmaf_rn(df, df, acc_c);
+                    }
+                }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-            if (lane == 0)
-                keys[r0 + rr] = id < (uint32_t)A.n ? ((unsigned long long)__float_as_uint(acc) << 32) | id : ~0ull;
+            for (int o = 4; o > 0; o >>= 1) {
+                acc_a = __fadd_rn(acc_a, __shfl_xor_sync(0xffffffffu, acc_a, o));
+                acc_c = __fadd_rn(acc_c, __shfl_xor_sync(0xffffffffu, acc_c, o));
+            }
+            if (gl == 0) {
+                if (ra < mine) keys[ra] = va ? ((unsigned long long)__float_as_uint(acc_a) << 32) | ida : ~0ull;
+                if (rc < mine) keys[rc] = vc ? ((unsigned long long)__float_as_uint(acc_c) << 32) | idc : ~0ull;
+            }
         }
-        __syncthreads();  // this half may be refilled two rounds later
     }
+    __syncthreads();
 
     // local top-k: a linear bucket histogram of the distances finds a bucket
     // that holds the k-th smallest; only keys up to it are sorted
@@ -1224,28 +1323,36 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, in
     A.o_hist = (uint32_t)o;
     o = align16(o + 4ull * (256 + 64));
     A.o_misc = (uint32_t)o;
-    o = align16(o + 4ull * 128);
+    o = align16(o + 4ull * 160);
     A.o_cnt = (uint32_t)o;
     o = align16(o + 4ull * NC * (1 + CL + NT / 32));
-    A.o_seg = (uint32_t)o;  // S4 segment list; later CTA 0's inbox of the CL local top-k lists
-    o = align16(o + std::max<uint64_t>(4ull * (2 * MAXSEG + 1), 8ull * CL * k));
-    A.o_slots = (uint32_t)o;
-    o = align16(o + 4ull * A.per_cta);
+    // S4's segment list; from S5 on, CTA 0's inbox of the CL local top-k lists
+    // followed by this CTA's candidate slots
+    A.o_seg = (uint32_t)o;
+    A.o_slots = (uint32_t)(o + align16(8ull * CL * k));
+    o = align16(o + std::max<uint64_t>(8ull * MAXSEG + 4ull * (MAXSEG + 1), align16(8ull * CL * k) + 4ull * A.per_cta));
     A.sortP = next_pow2(std::max<uint32_t>(A.per_cta, 1));
     A.o_union = (uint32_t)o;
     A.nbits = nsmax == 8 ? 4 : (nsmax == 16 ? 5 : 6);
-    const uint64_t plane_bytes = 4ull * A.nbits * A.G;
+    // S4 counters: nibble sets of up to 15 subspaces, then one-bit planes for
+    // the last few (a second set only when 4 or more subspaces remain)
+    {
+        const int Ns = ix->Ns;
+        A.nsets = (Ns <= 15 || Ns - 15 <= 3) ? 1u : 2u;
+        A.nplanes = (uint32_t)std::max(0, Ns - 15 * (int)A.nsets);
+        A.nstore = std::max(A.nbits, 4u * A.nsets + A.nplanes);
+    }
+    const uint64_t plane_bytes = 4ull * A.nstore * A.G;
     const uint64_t cent_bytes = 8ull * sk * ix->hmax;
     A.stage_cent = cent_bytes <= 65536 ? 1u : 0u;
     const uint64_t s3_bytes = S3_BYTES + (A.stage_cent ? cent_bytes : 0);
-    const uint64_t row_bytes = 4ull * ix->ld;
-    // S6 reuses the union: the row double buffer (or, after it, the distance
-    // histogram and survivors) at its start, the CTA's re-rank keys at its end
+    // S6 reuses the union: the distance histogram and survivors at its start,
+    // the CTA's re-rank keys at its end
     const uint64_t keys_bytes = align16(8ull * A.sortP);
-    const uint64_t s6_bytes = std::max<uint64_t>(4ull * NB + 8ull * SURV_CAP, 2 * 8 * row_bytes) + keys_bytes;
+    const uint64_t s6_bytes = 4ull * NB + 8ull * SURV_CAP + keys_bytes;
     const uint64_t ubytes = align16(std::max(plane_bytes, std::max(s3_bytes, s6_bytes)));
     A.o_keys = (uint32_t)(o + ubytes - keys_bytes);
-    A.rows_half = (uint32_t)std::max<uint64_t>(1, (ubytes - keys_bytes) / 2 / row_bytes);
+
     o = align16(o + ubytes);
     L->smem = o;
     return SUCO_OK;
@@ -1386,6 +1493,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     A.beta_per = p->beta_per_query;
     A.out_ids = ids;
     A.out_dist = dist;
+
     if (dbg) {
         A.dbg_teff = dbg->t_eff;
         A.dbg_act = dbg->activated;
