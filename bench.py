@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--threads", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--recall-sample", type=int, default=256)
+    p.add_argument("--plain", action="store_true", help="time the fixed-ratio path at the workload's own alpha and "
+                   "beta even where the workload trains the ratio network")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
     return p.parse_args()
 
 
@@ -147,7 +150,10 @@ def algorithmic_bytes_per_query(w, T, C, teff_mean_total):
     return 4.0 * teff_mean_total + 4.0 * C * w.d
 
 
-def run_cpu_baseline(w, X, Q, sample_q, threads, alpha=None, beta=None):
+def run_cpu_baseline(w, X, Q, threads, alpha=None, beta=None, target_s=15.0):
+    """The FP64 oracle on the host cores over a bounded sample of the same
+    workload: a probe of 2*threads queries sizes the sample to about
+    target_s seconds of CPU work."""
     import oracle
     alpha = w.alpha if alpha is None else alpha
     beta = w.beta if beta is None else beta
@@ -158,14 +164,19 @@ def run_cpu_baseline(w, X, Q, sample_q, threads, alpha=None, beta=None):
     idx = oracle.build_index(X, w.Ns, w.sqrtK, 2, W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK),
                              nthreads=threads)
     build_s = time.time() - t0
+    probe = min(len(Q), 2 * threads)
+    t0 = time.time()
+    oracle.query_batch(X, idx, Q[:probe], w.k, T, C, rank_precision=0, nthreads=threads)
+    per_q = (time.time() - t0) / probe
+    sample_q = int(min(len(Q), max(probe, round(target_s / max(per_q, 1e-9)))))
     t0 = time.time()
     oracle.query_batch(X, idx, Q[:sample_q], w.k, T, C, rank_precision=0, nthreads=threads)
     dt = time.time() - t0
     return {"value": sample_q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{sample_q} queries of the same workload at alpha={alpha}, beta={beta}, FP64 oracle "
-                      f"(Algorithms 3-4), OpenMP over queries "
-                      f"on {threads} host threads; oracle index built with 2 Lloyd iterations in {build_s:.1f}s "
-                      f"(index build not timed)", "seconds": dt}
+            "sample": f"the first {sample_q} of the {len(Q)} queries of the same workload at alpha={alpha}, "
+                      f"beta={beta}, FP64 oracle (Algorithms 3-4), OpenMP over queries on {threads} host threads; "
+                      f"oracle index built with 2 Lloyd iterations in {build_s:.1f}s (index build not timed)",
+            "seconds": dt}
 
 
 def run_reference(args):
@@ -391,7 +402,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as _o
         pa, pb = (plain["alpha"], plain["beta"]) if plain else (w.alpha, w.beta)
-        cpu = run_cpu_baseline(w, X, Qall, 32, _o.max_threads(), alpha=pa, beta=pb)
+        cpu = run_cpu_baseline(w, X, Qall, _o.max_threads(), alpha=pa, beta=pb, target_s=args.cpu_seconds)
 
     if rank == 0:
         cfg = workload_config(w, B)
@@ -433,7 +444,7 @@ def main():
     dev = torch.device("cuda", local_rank)
     pkg.load_library()
     w = W.WORKLOADS[args.workload]
-    if w.n_train:
+    if w.n_train and not args.plain:
         run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev)
         if world > 1:
             tdist.destroy_process_group()
@@ -573,7 +584,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as _o
         threads = _o.max_threads()
-        cpu = run_cpu_baseline(w, X, Qall, 64, threads)
+        cpu = run_cpu_baseline(w, X, Qall, threads, target_s=args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

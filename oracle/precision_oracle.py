@@ -1,0 +1,127 @@
+"""Reduced-precision copies of the dataset and the coarse re-rank (TEST INFRASTRUCTURE).
+
+The paper computes in full precision.  The query path also offers a
+reduced-precision re-rank: candidate rows are read from a BF16 (or FP8 E4M3,
+with one scale per subspace) copy of the dataset, the R candidates with the
+smallest coarse squared distance survive, and those are re-ranked exactly.
+This module restates that computation in FP64 with NumPy, from the number
+formats' definitions:
+
+  - bfloat16: the upper 16 bits of an IEEE binary32 value after rounding to
+    nearest, ties to even, on the dropped 16 bits (8 significant bits);
+  - E4M3 (the "fn" variant): 1 sign bit, 4 exponent bits with bias 7, 3
+    mantissa bits; exponent 0 encodes subnormals m/8 * 2^-6; the code with
+    all exponent and mantissa bits set is NaN; there is no infinity and the
+    largest finite magnitude is 448.  Rounding is to nearest, ties to even,
+    and magnitudes beyond 448 saturate to 448.
+
+Coarse distance of a candidate row x to the query q: sum_j (xhat_j - q_j)^2,
+xhat the decoded reduced-precision row (times the subspace scale for E4M3).
+Survivors: the first min(R, C) candidates by (coarse distance, id).  Result:
+the k survivors nearest by exact squared distance, ties by id.
+"""
+import numpy as np
+
+from . import suco_oracle as _o
+
+
+def round_bf16(x):
+    """FP32 -> bfloat16 bit patterns (uint16), round to nearest even."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    nan = np.isnan(np.asarray(x, dtype=np.float32))
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF
+    r = np.where(nan, (u >> 16) | 0x40, r)  # keep NaN a (quiet) NaN
+    return r.astype(np.uint16)
+
+
+def bf16_to_f64(b):
+    return (np.asarray(b, dtype=np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def e4m3_values():
+    """Value of each of the 256 E4M3 codes (NaN for the two NaN codes)."""
+    v = np.empty(256, dtype=np.float64)
+    for c in range(256):
+        s = -1.0 if c & 0x80 else 1.0
+        e = (c >> 3) & 0xF
+        m = c & 0x7
+        if e == 0xF and m == 0x7:
+            v[c] = np.nan
+        elif e == 0:
+            v[c] = s * (m / 8.0) * 2.0 ** -6
+        else:
+            v[c] = s * (1.0 + m / 8.0) * 2.0 ** (e - 7)
+    return v
+
+
+def quantize_e4m3(x):
+    """float -> E4M3 codes (uint8): nearest finite value, ties to the even
+    code (mantissa LSB 0), magnitudes beyond 448 saturated."""
+    vals = e4m3_values()
+    finite = np.where(~np.isnan(vals))[0]
+    fv = vals[finite]
+    x = np.clip(np.asarray(x, dtype=np.float64), -448.0, 448.0)
+    flat = x.reshape(-1)
+    out = np.empty(flat.shape, dtype=np.uint8)
+    for i, t in enumerate(flat):
+        err = np.abs(fv - t)
+        best = np.flatnonzero(err == err.min())
+        codes = finite[best]
+        if len(codes) > 1:  # a tie between two neighbours (or +0 / -0): the even one
+            even = codes[(codes & 1) == 0]
+            codes = even if len(even) else codes
+            if t >= 0:
+                codes = codes[(codes & 0x80) == 0] if np.any((codes & 0x80) == 0) else codes
+            else:
+                codes = codes[(codes & 0x80) != 0] if np.any((codes & 0x80) != 0) else codes
+        out[i] = codes[0]
+    return out.reshape(x.shape)
+
+
+def e4m3_to_f64(c):
+    return e4m3_values()[np.asarray(c, dtype=np.int64)]
+
+
+def subspace_scales_e4m3(X, Ns):
+    """One scale per subspace: the largest |x| over the subspace's columns
+    divided by 448 (1 where the subspace is all zero)."""
+    X = np.asarray(X, dtype=np.float64)
+    d = X.shape[1]
+    s = np.empty(Ns, dtype=np.float64)
+    for i in range(Ns):
+        off, ln = _o.subspace_dims(d, Ns, i)
+        m = np.abs(X[:, off:off + ln]).max() if X.shape[0] else 0.0
+        s[i] = m / 448.0 if m > 0 else 1.0
+    return s
+
+
+def column_scales(scales, d, Ns):
+    col = np.empty(d, dtype=np.float64)
+    for i in range(Ns):
+        off, ln = _o.subspace_dims(d, Ns, i)
+        col[off:off + ln] = scales[i]
+    return col
+
+
+def decoded_rows(X, precision, Ns=None, scales=None):
+    """Rows as the coarse pass sees them: 1 = BF16, 2 = E4M3 times the
+    per-subspace scale."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    if precision == 1:
+        return bf16_to_f64(round_bf16(X))
+    if precision == 2:
+        col = column_scales(scales, X.shape[1], Ns)
+        return e4m3_to_f64(quantize_e4m3(X.astype(np.float64) / col[None, :])) * col[None, :]
+    raise ValueError(precision)
+
+
+def coarse_rerank(X, Xhat_rows, q, cands, R, k):
+    """Survivors and final top-k of the reduced-precision re-rank.
+    Xhat_rows: decoded rows of the candidates (same order as cands)."""
+    cands = np.asarray(cands, dtype=np.int64)
+    q64 = np.asarray(q, dtype=np.float64)
+    coarse = ((np.asarray(Xhat_rows, dtype=np.float64) - q64[None, :]) ** 2).sum(axis=1)
+    order = np.lexsort((cands, coarse))
+    surv = cands[order[:min(int(R), len(cands))]]
+    ids, dist = _o.rerank(X, q, surv, k)
+    return dict(survivors=surv, coarse=coarse, coarse_order=order, ids=ids, dist=dist)

@@ -1,0 +1,94 @@
+"""Pins of the reduced-precision oracle (oracle/precision_oracle.py) against
+the number formats' definitions, library conversions and closed forms."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import precision_oracle as P
+
+torch = pytest.importorskip("torch")
+
+
+def test_bf16_rounding_matches_torch_round_to_nearest_even():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(50_000) * 1e3, rng.standard_normal(50_000) * 1e-30,
+                        [0.0, -0.0, 1.0, 255.0, 3.4e38, -3.4e38, np.inf, -np.inf]]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(P.round_bf16(x), ref)
+
+
+def test_bf16_ties_go_to_even():
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: rounds down to the even 1.0;
+    # 1 + 3*2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6: rounds up to the even one
+    x = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8], dtype=np.float32)
+    np.testing.assert_array_equal(P.bf16_to_f64(P.round_bf16(x)), [1.0, 1 + 2.0 ** -6])
+
+
+def test_bf16_is_exact_on_small_integers():
+    x = np.arange(0, 257, dtype=np.float32)
+    np.testing.assert_array_equal(P.bf16_to_f64(P.round_bf16(x)), x.astype(np.float64))
+
+
+def test_e4m3_table_closed_form():
+    v = P.e4m3_values()
+    assert np.nanmax(v) == 448.0 and np.nanmin(v) == -448.0
+    assert v[0x01] == 2.0 ** -9          # smallest subnormal
+    assert v[0x08] == 2.0 ** -6          # smallest normal
+    assert v[0x38] == 1.0
+    assert np.isnan(v[0x7F]) and np.isnan(v[0xFF])
+    assert np.isfinite(v).sum() == 254
+
+
+def test_e4m3_quantisation_matches_torch_cast():
+    rng = np.random.default_rng(1)
+    v = P.e4m3_values()
+    fin = v[np.isfinite(v)]
+    mids = ((np.sort(fin)[1:] + np.sort(fin)[:-1]) / 2.0)  # every tie point
+    x = np.concatenate([rng.uniform(-440, 440, 3000), rng.uniform(-1, 1, 2000) * 2.0 ** -5, mids]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    got = P.quantize_e4m3(x.astype(np.float64))
+    # +0 / -0 are both exact for a zero tie; compare values
+    np.testing.assert_array_equal(P.e4m3_to_f64(got), P.e4m3_to_f64(ref))
+
+
+def test_e4m3_saturates():
+    np.testing.assert_array_equal(P.e4m3_to_f64(P.quantize_e4m3(np.array([1e6, -1e6, 449.0]))), [448.0, -448.0, 448.0])
+
+
+def test_coarse_rerank_with_all_survivors_is_the_exact_rerank():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((500, 24)).astype(np.float32)
+    q = rng.standard_normal(24).astype(np.float32)
+    cands = rng.choice(500, 120, replace=False)
+    Xh = P.decoded_rows(X[cands], 1)
+    out = P.coarse_rerank(X, Xh, q, cands, R=10_000, k=7)
+    ids, dist = oracle.rerank(X, q, cands, 7)
+    assert np.array_equal(out["ids"], ids)
+    np.testing.assert_array_equal(out["dist"], dist)
+
+
+def test_coarse_rerank_on_exactly_representable_data_keeps_the_true_nearest():
+    # integer rows <= 256 are exact in BF16: coarse = exact distance, so the
+    # R survivors are the R nearest candidates and the top-k is the exact top-k
+    rng = np.random.default_rng(3)
+    X = rng.integers(0, 256, size=(800, 16)).astype(np.float32)
+    q = rng.integers(0, 256, size=16).astype(np.float32)
+    cands = np.arange(800)
+    out = P.coarse_rerank(X, P.decoded_rows(X, 1), q, cands, R=20, k=5)
+    exact = ((X.astype(np.float64) - q) ** 2).sum(1)
+    order = np.lexsort((cands, exact))
+    assert np.array_equal(np.sort(out["survivors"]), np.sort(cands[order[:20]]))
+    assert np.array_equal(out["ids"], cands[order[:5]])
+
+
+def test_e4m3_rows_use_one_scale_per_subspace():
+    rng = np.random.default_rng(4)
+    X = np.abs(rng.standard_normal((300, 12))).astype(np.float32)
+    X[:, 8:] *= 1000.0  # subspace 2 of 3 has a much larger range
+    s = P.subspace_scales_e4m3(X, 3)
+    assert s[2] == pytest.approx(np.abs(X[:, 8:]).max() / 448.0)
+    Xh = P.decoded_rows(X, 2, Ns=3, scales=s)
+    # relative error of a normal E4M3 value is at most 2^-4
+    big = np.abs(X) > 2.0 ** -6 * np.repeat(s, 4)[None, :]
+    rel = np.abs(Xh - X)[big] / np.abs(X)[big]
+    assert rel.max() <= 2.0 ** -4 + 1e-12
