@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--plain", action="store_true", help="time the fixed-ratio path at the workload's own alpha and "
                    "beta even where the workload trains the ratio network")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
+    p.add_argument("--exact-rerank", type=int, default=512, help="survivors of the BF16 coarse re-rank")
     return p.parse_args()
 
 
@@ -271,10 +272,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     target = args.target_recall
     stream = torch.cuda.current_stream(dev)
 
-    # learned operating point: the smallest margin reaching the target
-    margin, rec_learned = L.tune_offsets(index, model, Qe, gt, w.k, target=target)
-    model.offsets = (margin, margin)
-    note(f"learned operating point: margin {margin}, recall {rec_learned:.4f}")
+    pkg.suco_add_reduced_copies(index)  # BF16 copy of the dataset for the coarse re-rank
     B = w.batch
     nb = (w.nq + B - 1) // B
     batches = [Qe[i * B:(i + 1) * B] for i in range(nb)]
@@ -282,17 +280,36 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     outs = [(torch.empty((b.shape[0], w.k), dtype=torch.int32, device=dev),
              torch.empty((b.shape[0], w.k), dtype=torch.float32, device=dev)) for b in batches]
     ab = [(torch.empty(b.shape[0], device=dev), torch.empty(b.shape[0], device=dev)) for b in batches]
-    st = model.struct()
+    cur = {}
 
     def learned_step(s, ev, q=None):
         bi = order[s % nb]
         qb = batches[bi] if q is None else q
-        pkg.suco_mlp_predict(index, st, qb, alpha=ab[bi][0], beta=ab[bi][1], stream=stream)
+        pkg.suco_mlp_predict(index, cur["st"], qb, alpha=ab[bi][0], beta=ab[bi][1], stream=stream)
         if ev:
             ev[0].record(stream)
         pkg.suco_query_batch(index, qb, w.k, L.FALLBACK[0], L.BETA_RANGE[1], out_ids=outs[bi][0],
-                             out_dist=outs[bi][1], alpha_per_query=ab[bi][0], beta_per_query=ab[bi][1], stream=stream)
+                             out_dist=outs[bi][1], alpha_per_query=ab[bi][0], beta_per_query=ab[bi][1], stream=stream,
+                             precision=cur["precision"], exact_rerank=args.exact_rerank)
         return qb.shape[0]
+
+    # learned operating point per re-rank precision: the smallest margin that
+    # reaches the target; the faster of the two precisions is the learned arm
+    by_prec = {}
+    for prec in ("fp32", "bf16"):
+        m, r = L.tune_offsets(index, model, Qe, gt, w.k, target=target, precision=prec,
+                              exact_rerank=args.exact_rerank)
+        model.offsets = (m, m)
+        cur.update(st=model.struct(), precision=prec)
+        ms, _ = time_loop(torch, stream, 2 * nb, 2, learned_step)
+        by_prec[prec] = {"margin": m, "recall_at_k": r, "qps_probe": 2 * w.nq / (ms / 1000.0)}
+        note(f"learned {prec}: margin {m}, recall {r:.4f}, probe {by_prec[prec]['qps_probe']:.0f} q/s")
+    ok = [p for p in by_prec if by_prec[p]["recall_at_k"] >= target] or list(by_prec)
+    learned_prec = max(ok, key=lambda p: by_prec[p]["qps_probe"])
+    margin, rec_learned = by_prec[learned_prec]["margin"], by_prec[learned_prec]["recall_at_k"]
+    model.offsets = (margin, margin)
+    cur.update(st=model.struct(), precision=learned_prec)
+    st = cur["st"]
 
     def plain_step_fn(alpha, beta):
         def f(s, ev):
@@ -375,7 +392,9 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
         e2e_value = float(sm[1]) / (float(mx[0]) / 1000.0)
 
     # roofline of the query kernel: per query 4 * sum_i T_eff,i id bytes and
-    # 4 * C_b * d row bytes, C_b from the query's own beta
+    # 4 * C_b * d row bytes, C_b from the query's own beta (with the BF16
+    # re-rank: 2 * C_b * d coarse bytes and 4 * min(R, C_b) * d exact bytes)
+    R = args.exact_rerank or 512
     bytes_steps = 0.0
     per_batch = {}
     for bi in set(order[(args.warmup + s) % nb] for s in range(args.steps)):
@@ -383,9 +402,13 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
         dbg = pkg.suco_query_debug(index, batches[bi], w.k, L.FALLBACK[0], L.BETA_RANGE[1], want=("t_eff",),
                                    alpha_per_query=al, beta_per_query=be)
         teff = float(dbg["t_eff"].double().sum().item())
-        Cs = sum(pkg.suco_thresholds(w.n, L.FALLBACK[0], min(float(x), L.BETA_RANGE[1]), w.k)[1]
-                 for x in be.cpu().numpy())
-        per_batch[bi] = 4.0 * teff + 4.0 * Cs * w.d
+        Cs = [pkg.suco_thresholds(w.n, L.FALLBACK[0], min(float(x), L.BETA_RANGE[1]), w.k)[1]
+              for x in be.cpu().numpy()]
+        if learned_prec == "bf16":
+            rows = sum((2.0 * c + 4.0 * R) * w.d if c > R else 4.0 * c * w.d for c in Cs)
+        else:
+            rows = sum(4.0 * c * w.d for c in Cs)
+        per_batch[bi] = 4.0 * teff + rows
     for s in range(args.steps):
         bytes_steps += per_batch[order[(args.warmup + s) % nb]]
     peaks = measured_peaks()
@@ -395,7 +418,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     achieved = bytes_steps / args.steps / (query_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": committed_traffic(w.number), "peak_source": peak_src,
-                "kernel": "suco_query_kernel (learned per-query alpha/beta, one launch per batch)",
+                "kernel": f"suco_query_kernel (learned per-query alpha/beta, {learned_prec} re-rank, one launch per batch)",
                 "algorithmic_bytes_per_query": bytes_steps / sum(nq_step), "mean_launch_ms": query_ms}
 
     cpu = None
@@ -407,13 +430,16 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     if rank == 0:
         cfg = workload_config(w, B)
         cfg["workload"] = (f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, k={w.k}, learned per-query "
-                           f"alpha/beta (MLP {3 * w.Ns}-{model.H}-2, GELU, BF16 weights), FP32 distances")
+                           f"alpha/beta (MLP {3 * w.Ns}-{model.H}-2, GELU, BF16 weights), "
+                           + ("FP32 re-rank" if learned_prec == "fp32" else
+                              f"BF16 coarse re-rank + exact FP32 re-rank of the top {R}"))
         cfg["n_train"] = n_train
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "recall_at_k": rec_learned, "k": w.k, "target_recall": target,
-                "margin": margin, "plain_fp32": plain_line,
+                "margin": margin, "learned_precision": learned_prec, "learned_by_precision": by_prec,
+                "plain_fp32": plain_line,
                 "speedup_vs_plain": (value / plain_line["value"]) if plain_line else None,
                 "predict_ms_per_step": predict_ms, "query_ms_per_step": query_ms,
                 "roofline": roofline, "cpu_baseline": cpu,

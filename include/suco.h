@@ -112,6 +112,17 @@ SUCO_API int suco_build_index_from_assignments(const float* data, int64_t n, int
  * this flag launches one cluster per query instead. */
 #define SUCO_QUERY_ONE_CLUSTER_PER_QUERY 1
 
+/* suco_query_params.precision: how the beta*n candidates are re-ranked.
+ * FP32 computes every candidate's exact squared distance (Algorithm 4).
+ * BF16 (not in the paper) first computes a coarse squared distance of every
+ * candidate from the index's BF16 copy of D (values decoded exactly, sums in
+ * FP32); the exact_rerank candidates with the smallest (coarse distance, id)
+ * over the whole query survive, and only they are re-ranked by exact FP32
+ * distance.  When C <= exact_rerank every candidate survives and the result
+ * equals FP32's. */
+#define SUCO_PRECISION_FP32 0
+#define SUCO_PRECISION_BF16 1
+
 typedef struct suco_query_params {
     int32_t k;            /* results per query (the maximum if k_per_query), 1..256   */
     int32_t cluster_size; /* CTAs cooperating on one query (1,2,4,8,16); 0 = automatic  */
@@ -122,6 +133,8 @@ typedef struct suco_query_params {
     const int32_t* k_per_query;    /* (device, nullable) [nq], clamped to [1, k]        */
     const float* alpha_per_query;  /* (device, nullable) [nq], clamped to (0, 1]        */
     const float* beta_per_query;   /* (device, nullable) [nq], clamped to (0, beta]     */
+    int32_t precision;    /* SUCO_PRECISION_*; BF16 needs suco_add_reduced_copies      */
+    int32_t exact_rerank; /* R: survivors of the coarse pass (0 = 512), up to 2^24       */
 } suco_query_params;
 
 /* Answers nq queries (Algorithm 4; Algorithm 3 for the cell walk).
@@ -144,11 +157,22 @@ typedef struct suco_query_debug_out {
     uint8_t* scores;     /* (device) [nq][n] SC-scores (Definition 4)                      */
     int32_t* cands;      /* (device) [nq][C] candidate ids: the ids scoring above the cut in
                             ascending id order, then the lowest-id ties at the cut         */
+    uint8_t* survivors;  /* (device) [nq][n], zeroed by the caller: set to 1 for every
+                            candidate that survives the BF16 coarse pass                    */
 } suco_query_debug_out;
 
 /* suco_query_batch plus the per-stage outputs above (same arguments). */
 SUCO_API int suco_query_debug(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
                      int32_t* out_ids, float* out_dist, const suco_query_debug_out* debug, void* stream);
+
+/* Adds reduced-precision copies of the index's dataset (no counterpart in the
+ * paper).  mask bit 0 (SUCO_COPY_BF16): D rounded to BF16 (round to nearest,
+ * ties to even), n x ceil8(d) 16-bit values, zero padded; it serves queries
+ * with precision SUCO_PRECISION_BF16.  A copy that exists is kept.  Allocates
+ * device memory; synchronous.  Errors: SUCO_EINVAL (NULL index, unknown bits),
+ * SUCO_ENOMEM, SUCO_ECUDA. */
+#define SUCO_COPY_BF16 1
+SUCO_API int suco_add_reduced_copies(suco_index* index, int32_t mask, void* stream);
 
 /* Times every launch shape (cluster size x threads per CTA) that fits, on the
  * given queries and parameters (which must leave cluster_size and threads at

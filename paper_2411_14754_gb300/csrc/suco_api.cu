@@ -69,6 +69,8 @@ void free_index_memory(DeviceIndex* ix)
     cudaFree(ix->perm);
     cudaFree(ix->split);
     cudaFree(ix->work);
+    cudaFree(ix->Xh);
+    ix->Xh = nullptr;
     ix->work = nullptr;
     ix->X = nullptr;
     ix->cent = nullptr;
@@ -144,6 +146,12 @@ int check_query_params(const suco_index* index, const float* queries, int64_t nq
     if (!(p->alpha > 0.0 && p->alpha <= 1.0)) return fail(SUCO_EINVAL, "alpha=%g must be in (0, 1]", p->alpha);
     if (!(p->beta > 0.0 && p->beta <= 1.0)) return fail(SUCO_EINVAL, "beta=%g must be in (0, 1]", p->beta);
     if (p->flags & ~SUCO_QUERY_ONE_CLUSTER_PER_QUERY) return fail(SUCO_EINVAL, "unknown flags 0x%x", p->flags);
+    if (p->precision != SUCO_PRECISION_FP32 && p->precision != SUCO_PRECISION_BF16)
+        return fail(SUCO_EINVAL, "precision=%d must be SUCO_PRECISION_FP32 or SUCO_PRECISION_BF16", p->precision);
+    if (p->precision == SUCO_PRECISION_BF16 && !index->ix.Xh)
+        return fail(SUCO_ESTATE, "the index has no BF16 copy: call suco_add_reduced_copies first");
+    if (p->exact_rerank < 0 || p->exact_rerank > (1 << 24))
+        return fail(SUCO_EINVAL, "exact_rerank=%d must be in [0, 2^24]", p->exact_rerank);
     if (nq > 0 && (!queries || !ids || !dist)) return fail(SUCO_EINVAL, "queries/out_ids/out_dist must not be NULL");
     return SUCO_OK;
 }

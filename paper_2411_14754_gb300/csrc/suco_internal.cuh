@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,8 @@ struct DeviceIndex {
     int64_t ld = 0;     // row stride of X in floats (d rounded up to 4)
     int64_t n_ch = 0;   // ids per chunk
     float* X = nullptr;           // [n][ld]; columns d..ld-1 are zero
+    uint16_t* Xh = nullptr;       // optional BF16 copy of X, [n][ldh] (ldh = d rounded up to 8), padding zero
+    int64_t ldh = 0;
     float* cent = nullptr;        // [Ns][2][sqrtK][hmax]; padding zero
     uint32_t* cell_off = nullptr; // [Ns][K+1] offsets into perm[i]
     int32_t* perm = nullptr;      // [Ns][n] ids grouped by cell, ascending inside a cell

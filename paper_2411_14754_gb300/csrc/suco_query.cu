@@ -81,6 +81,13 @@ struct QArgs {
     uint32_t span, G;  // ids per CTA, 32-id groups per CTA
     uint32_t nbits;    // B: bit planes of the sliced SC-score counts
     uint32_t nsets, nplanes, nstore;  // S4 counters: 4-bit nibble sets, one-bit planes, words per 32 ids
+    const uint16_t* __restrict__ Xh;   // BF16 copy of X, [n][ldh] (precision 1)
+    int64_t ldh;
+    int64_t ldq;                       // staged query length (d rounded up to 16, zero padded)
+    int32_t precision;                 // 0 exact FP32 re-rank; 1 BF16 coarse pass, then FP32 on R survivors
+    uint32_t R;                        // survivors of the coarse pass
+    uint8_t* dbg_surv;                 // [nq][n] 1 for the coarse pass's survivors (debug)
+    uint32_t o_rsel;                   // [2][256] published radix histograms of the survivor cut
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -764,6 +771,230 @@ __device__ __forceinline__ uint32_t bitsliced_ge(const uint32_t acc[B], uint32_t
     return ge;
 }
 
+// S6 exact pass: FP32 squared distances of the rows listed in ids[0, count)
+// into keys (distance bits << 32 | id; ~0 for an id outside [0, n)).  8 lanes
+// per row, two groups of 4 rows per warp in flight; each lane keeps S6_CH
+// float4 chunks of each of its two rows in registers per load round.
+template <int NT>
+__device__ void rerank_fp32(const QArgs& A, const float4* q4, const uint32_t* ids, uint32_t count,
+                            unsigned long long* keys)
+{
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane >> 3, gl = lane & 7;
+    const int ld4 = (int)(A.ld / 4);
+    const float4* X4 = reinterpret_cast<const float4*>(A.X);
+    for (uint32_t rb = (uint32_t)warp * 8u; rb < count; rb += (uint32_t)NW * 8u) {
+        const uint32_t ra = rb + (uint32_t)grp, rc = ra + 4u;
+        const uint32_t ida = ra < count ? ids[ra] : 0xffffffffu;
+        const uint32_t idc = rc < count ? ids[rc] : 0xffffffffu;
+        const bool va = ida < (uint32_t)A.n, vc = idc < (uint32_t)A.n;
+        const float4* pa = X4 + (int64_t)(va ? ida : 0u) * ld4;
+        const float4* pc = X4 + (int64_t)(vc ? idc : 0u) * ld4;
+        float acc_a = 0.f, acc_c = 0.f;
+        for (int c0 = gl; c0 < ld4; c0 += 8 * S6_CH) {
+            float4 xa[S6_CH], xc[S6_CH];
+#pragma unroll
+            for (int u = 0; u < S6_CH; ++u) {
+                const int c = c0 + 8 * u;
+                xa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                xc[u] = xa[u];
+                if (c < ld4) {
+                    if (va) xa[u] = ldg_stream(pa + c);
+                    if (vc) xc[u] = ldg_stream(pc + c);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < S6_CH; ++u) {
+                const int c = c0 + 8 * u;
+                if (c < ld4) {
+                    const float4 qv = q4[c];
+                    float df = __fsub_rn(xa[u].x, qv.x);
+                    acc_a = __fmaf_rn(df, df, acc_a);
+                    df = __fsub_rn(xa[u].y, qv.y);
+                    acc_a = __fmaf_rn(df, df, acc_a);
+                    df = __fsub_rn(xa[u].z, qv.z);
+                    acc_a = __fmaf_rn(df, df, acc_a);
+                    df = __fsub_rn(xa[u].w, qv.w);
+                    acc_a = __fmaf_rn(df, df, acc_a);
+                    df = __fsub_rn(xc[u].x, qv.x);
+                    acc_c = __fmaf_rn(df, df, acc_c);
+                    df = __fsub_rn(xc[u].y, qv.y);
+                    acc_c = __fmaf_rn(df, df, acc_c);
+                    df = __fsub_rn(xc[u].z, qv.z);
+                    acc_c = __fmaf_rn(df, df, acc_c);
+                    df = __fsub_rn(xc[u].w, qv.w);
+                    acc_c = __fmaf_rn(df, df, acc_c);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            acc_a = __fadd_rn(acc_a, __shfl_xor_sync(0xffffffffu, acc_a, o));
+            acc_c = __fadd_rn(acc_c, __shfl_xor_sync(0xffffffffu, acc_c, o));
+        }
+        if (gl == 0) {
+            if (ra < count) keys[ra] = va ? ((unsigned long long)__float_as_uint(acc_a) << 32) | ida : ~0ull;
+            if (rc < count) keys[rc] = vc ? ((unsigned long long)__float_as_uint(acc_c) << 32) | idc : ~0ull;
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 ldg_stream_u4(const uint4* p)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// adds the squared differences of the 8 BF16 values in w (element 2i in the
+// low half of word i) to q[0..8) into acc, in element order
+__device__ __forceinline__ float bf16x8_sqdiff(uint4 w, const float4* q, float acc)
+{
+    const float4 q0 = q[0], q1 = q[1];
+    const float x[8] = {__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xffff0000u),
+                        __uint_as_float(w.y << 16), __uint_as_float(w.y & 0xffff0000u),
+                        __uint_as_float(w.z << 16), __uint_as_float(w.z & 0xffff0000u),
+                        __uint_as_float(w.w << 16), __uint_as_float(w.w & 0xffff0000u)};
+    const float qq[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float df = __fsub_rn(x[j], qq[j]);
+        acc = __fmaf_rn(df, df, acc);
+    }
+    return acc;
+}
+
+// S6 coarse pass: squared distances of the BF16 copies of the rows listed in
+// ids[0, count), accumulated in FP32, into keys (same layout as rerank_fp32).
+template <int NT>
+__device__ void rerank_bf16(const QArgs& A, const float4* q4, const uint32_t* ids, uint32_t count,
+                            unsigned long long* keys)
+{
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane >> 3, gl = lane & 7;
+    const int ldc = (int)(A.ldh / 8);  // 16-byte chunks of 8 values per row
+    const uint4* X16 = reinterpret_cast<const uint4*>(A.Xh);
+    for (uint32_t rb = (uint32_t)warp * 8u; rb < count; rb += (uint32_t)NW * 8u) {
+        const uint32_t ra = rb + (uint32_t)grp, rc = ra + 4u;
+        const uint32_t ida = ra < count ? ids[ra] : 0xffffffffu;
+        const uint32_t idc = rc < count ? ids[rc] : 0xffffffffu;
+        const bool va = ida < (uint32_t)A.n, vc = idc < (uint32_t)A.n;
+        const uint4* pa = X16 + (int64_t)(va ? ida : 0u) * ldc;
+        const uint4* pc = X16 + (int64_t)(vc ? idc : 0u) * ldc;
+        float acc_a = 0.f, acc_c = 0.f;
+        for (int c0 = gl; c0 < ldc; c0 += 8 * S6_CH) {
+            uint4 xa[S6_CH], xc[S6_CH];
+#pragma unroll
+            for (int u = 0; u < S6_CH; ++u) {
+                const int c = c0 + 8 * u;
+                xa[u] = make_uint4(0u, 0u, 0u, 0u);
+                xc[u] = xa[u];
+                if (c < ldc) {
+                    if (va) xa[u] = ldg_stream_u4(pa + c);
+                    if (vc) xc[u] = ldg_stream_u4(pc + c);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < S6_CH; ++u) {
+                const int c = c0 + 8 * u;
+                if (c < ldc) {
+                    acc_a = bf16x8_sqdiff(xa[u], q4 + 2 * c, acc_a);
+                    acc_c = bf16x8_sqdiff(xc[u], q4 + 2 * c, acc_c);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            acc_a = __fadd_rn(acc_a, __shfl_xor_sync(0xffffffffu, acc_a, o));
+            acc_c = __fadd_rn(acc_c, __shfl_xor_sync(0xffffffffu, acc_c, o));
+        }
+        if (gl == 0) {
+            if (ra < count) keys[ra] = va ? ((unsigned long long)__float_as_uint(acc_a) << 32) | ida : ~0ull;
+            if (rc < count) keys[rc] = vc ? ((unsigned long long)__float_as_uint(acc_c) << 32) | idc : ~0ull;
+        }
+    }
+}
+
+// The key of rank R (1-based) among the keys of every CTA of the cluster
+// (keys are unique), by a radix select over 8-bit digits from the top: each
+// pass every CTA histograms its keys that match the decided prefix, publishes
+// the histogram, and after a cluster barrier every CTA sums the CL histograms
+// and picks the digit where the running count reaches R.  It stops as soon as
+// the whole crossing bin is needed, and returns the largest key of that bin,
+// so that exactly R keys of the cluster are <= the result.  Histograms
+// alternate between two published buffers: one is written while the previous
+// pass's is still read by the other CTAs.  Every CTA takes the same passes.
+template <int NT>
+__device__ unsigned long long cluster_rank_cut(const QArgs& A, char* smem, const unsigned long long* keys,
+                                               uint32_t count, uint32_t R)
+{
+    uint32_t* pub = reinterpret_cast<uint32_t*>(smem + A.o_rsel);   // [2][256]
+    uint32_t* tot = reinterpret_cast<uint32_t*>(smem + A.o_hist);   // [256] local sums
+    uint32_t* st = tot + 256;                                        // [0] digit, [1] below, [2] bin count
+    const int lane = threadIdx.x & 31;
+    const uint32_t CL = (uint32_t)A.CL;
+    unsigned long long prefix = 0ull, mask = 0ull;
+    uint32_t need = R;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 56 - 8 * pass;
+        uint32_t* h = pub + (pass & 1) * 256;
+        for (int t = threadIdx.x; t < 256; t += NT) h[t] = 0u;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < count; t += NT) {
+            const unsigned long long key = keys[t];
+            if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+        }
+        cluster_sync();
+        for (int t = threadIdx.x; t < 256; t += NT) {
+            const uint32_t a = smem_addr(h + t);
+            uint32_t sum = 0u;
+            for (uint32_t rr = 0; rr < CL; ++rr) sum += ld_cluster_u32(map_rank(a, rr));
+            tot[t] = sum;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t v[8], s = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = tot[lane * 8 + j];
+                s += v[j];
+            }
+            uint32_t incl = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t excl = incl - s;
+            if (excl < need && incl >= need) {
+                uint32_t cum = excl;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (cum + v[j] >= need) {
+                        st[0] = (uint32_t)(lane * 8 + j);
+                        st[1] = cum;
+                        st[2] = v[j];
+                        break;
+                    }
+                    cum += v[j];
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t digit = st[0], below = st[1], inbin = st[2];
+        __syncthreads();
+        prefix |= (unsigned long long)digit << shift;
+        mask |= 255ull << shift;
+        need -= below;
+        if (inbin == need) return prefix | (shift ? ((1ull << shift) - 1ull) : 0ull);
+    }
+    return prefix;
+}
+
 template <int NT, int NSMAX>
 __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const QArgs A)
 {
@@ -822,7 +1053,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     {
         float* qs = reinterpret_cast<float*>(smem + A.o_q);
         const float* qg = A.Q + b * A.d;
-        for (int j = threadIdx.x; j < A.ld; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
+        for (int j = threadIdx.x; j < A.ldq; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
         uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);
         for (int t = threadIdx.x; t < NC; t += NT) cnt[t] = 0u;
     }
@@ -1033,69 +1264,34 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     const uint32_t* slots = reinterpret_cast<const uint32_t*>(smem + A.o_slots);
     const uint32_t mine = qC > r * qper ? min(qper, qC - r * qper) : 0u;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + A.o_keys);  // [sortP]
-    const int ld4 = (int)(A.ld / 4);
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
-    // 8 lanes per row, two groups of 4 rows per warp in flight; each lane keeps
-    // S6_CH float4 chunks of each of its two rows in registers per load round
-    {
-        const int grp = lane >> 3, gl = lane & 7;
-        const float4* X4 = reinterpret_cast<const float4*>(A.X);
-        for (uint32_t rb = (uint32_t)warp * 8u; rb < mine; rb += (uint32_t)NW * 8u) {
-            const uint32_t ra = rb + (uint32_t)grp, rc = ra + 4u;
-            const uint32_t ida = ra < mine ? slots[ra] : 0xffffffffu;
-            const uint32_t idc = rc < mine ? slots[rc] : 0xffffffffu;
-            const bool va = ida < (uint32_t)A.n, vc = idc < (uint32_t)A.n;
-            const float4* pa = X4 + (int64_t)(va ? ida : 0u) * ld4;
-            const float4* pc = X4 + (int64_t)(vc ? idc : 0u) * ld4;
-            float acc_a = 0.f, acc_c = 0.f;
-            for (int c0 = gl; c0 < ld4; c0 += 8 * S6_CH) {
-                float4 xa[S6_CH], xc[S6_CH];
-#pragma unroll
-                for (int u = 0; u < S6_CH; ++u) {
-                    const int c = c0 + 8 * u;
-                    xa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    xc[u] = xa[u];
-                    if (c < ld4) {
-                        if (va) xa[u] = ldg_stream(pa + c);
-                        if (vc) xc[u] = ldg_stream(pc + c);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < S6_CH; ++u) {
-                    const int c = c0 + 8 * u;
-                    if (c < ld4) {
-                        const float4 qv = q4[c];
-                        float df = __fsub_rn(xa[u].x, qv.x);
-                        acc_a = __fmaf_rn(df, df, acc_a);
-                        df = __fsub_rn(xa[u].y, qv.y);
-                        acc_a = __fmaf_rn(df, df, acc_a);
-                        df = __fsub_rn(xa[u].z, qv.z);
-                        acc_a = __fmaf_rn(df, df, acc_a);
-                        df = __fsub_rn(xa[u].w, qv.w);
-                        acc_a = __fmaf_rn(df, df, acc_a);
-                        df = __fsub_rn(xc[u].x, qv.x);
-                        acc_c = __fmaf_rn(df, df, acc_c);
-                        df = __fsub_rn(xc[u].y, qv.y);
-                        acc_c = __fmaf_rn(df, df, acc_c);
-                        df = __fsub_rn(xc[u].z, qv.z);
-                        acc_c = __fmaf_rn(df, df, acc_c);
-                        df = __fsub_rn(xc[u].w, qv.w);
-                        acc_c = __fmaf_rn(df, df, acc_c);
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
-                acc_a = __fadd_rn(acc_a, __shfl_xor_sync(0xffffffffu, acc_a, o));
-                acc_c = __fadd_rn(acc_c, __shfl_xor_sync(0xffffffffu, acc_c, o));
-            }
-            if (gl == 0) {
-                if (ra < mine) keys[ra] = va ? ((unsigned long long)__float_as_uint(acc_a) << 32) | ida : ~0ull;
-                if (rc < mine) keys[rc] = vc ? ((unsigned long long)__float_as_uint(acc_c) << 32) | idc : ~0ull;
+    uint32_t nk = mine;  // keys of this CTA that enter the local top-k
+    if (A.precision == 0 || qC <= A.R) {
+        rerank_fp32<NT>(A, q4, slots, mine, keys);
+        __syncthreads();
+    } else {
+        // coarse pass on the reduced-precision copy, then the R smallest
+        // coarse keys of the whole cluster survive into the exact pass
+        rerank_bf16<NT>(A, q4, slots, mine, keys);
+        __syncthreads();
+        const unsigned long long cut = cluster_rank_cut<NT>(A, smem, keys, mine, A.R);
+        uint32_t* ns = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 106;
+        if (threadIdx.x == 0) *ns = 0u;
+        __syncthreads();
+        uint32_t* surv_ids = const_cast<uint32_t*>(slots);  // the candidate ids now live in the keys
+        for (uint32_t t = threadIdx.x; t < mine; t += NT) {
+            const unsigned long long key = keys[t];
+            if (key <= cut) {
+                const uint32_t id = (uint32_t)(key & 0xffffffffu);
+                surv_ids[atomicAdd(ns, 1u)] = id;
+                if (A.dbg_surv) A.dbg_surv[b * A.n + id] = 1u;
             }
         }
+        __syncthreads();
+        nk = *ns;
+        rerank_fp32<NT>(A, q4, surv_ids, nk, keys);
+        __syncthreads();
     }
-    __syncthreads();
 
     // local top-k: a linear bucket histogram of the distances finds a bucket
     // that holds the k-th smallest; only keys up to it are sorted
@@ -1106,11 +1302,11 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     const uint32_t kst = (uint32_t)A.k;
     unsigned long long* best = keys;  // sorted top-k ends up here
     uint32_t nbest = 0;
-    if (mine <= 2 * k || mine <= 64) {
-        for (uint32_t t = mine + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
+    if (nk <= 2 * k || nk <= 64) {
+        for (uint32_t t = nk + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
         __syncthreads();
         block_bitonic_sort<NT>(keys, (int)A.sortP);
-        nbest = min(k, mine);
+        nbest = min(k, nk);
     } else {
         if (threadIdx.x == 0) {
             kv[0] = 0xffffffffu;
@@ -1120,7 +1316,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         for (int t = threadIdx.x; t < NB; t += NT) khist[t] = 0u;
         __syncthreads();
         uint32_t lo = 0xffffffffu, hi = 0u;
-        for (uint32_t t = threadIdx.x; t < mine; t += NT) {
+        for (uint32_t t = threadIdx.x; t < nk; t += NT) {
             const unsigned long long v = keys[t];
             if (v == ~0ull) continue;
             const uint32_t db = (uint32_t)(v >> 32);
@@ -1133,7 +1329,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         const float dmin = __uint_as_float(kv[0]);
         const float drange = __fsub_rn(__uint_as_float(kv[1]), dmin);
         const float dscale = drange > 0.f ? __fdiv_rn((float)NB, drange) : 0.f;
-        for (uint32_t t = threadIdx.x; t < mine; t += NT) {
+        for (uint32_t t = threadIdx.x; t < nk; t += NT) {
             const unsigned long long v = keys[t];
             if (v != ~0ull) atomicAdd(&khist[value_bucket(__uint_as_float((uint32_t)(v >> 32)), dmin, dscale)], 1u);
         }
@@ -1165,7 +1361,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
             uint32_t* ctr = kv + 4;
             if (threadIdx.x == 0) *ctr = 0u;
             __syncthreads();
-            for (uint32_t t = threadIdx.x; t < mine; t += NT) {
+            for (uint32_t t = threadIdx.x; t < nk; t += NT) {
                 const unsigned long long v = keys[t];
                 if (v != ~0ull && (uint32_t)value_bucket(__uint_as_float((uint32_t)(v >> 32)), dmin, dscale) <= kb)
                     surv[atomicAdd(ctr, 1u)] = v;
@@ -1214,10 +1410,10 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
             nbest = min(k, ns);
         } else {
             // a crowded bucket (many equal distances): sort the whole share
-            for (uint32_t t = mine + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
+            for (uint32_t t = nk + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
             __syncthreads();
             block_bitonic_sort<NT>(keys, (int)A.sortP);
-            nbest = min(k, mine);
+            nbest = min(k, nk);
         }
     }
     // hand the sorted local list (padded to k) to CTA 0
@@ -1317,13 +1513,20 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, in
     uint64_t o = 0;
     A.o_tab = (uint32_t)o;
     A.tab_stride = align16(20 + 16ull * sk);
-    o = align16(o + (uint64_t)ix->Ns * A.tab_stride);
+    // the radix histograms of the survivor cut (S6) reuse the subspace tables'
+    // region: no CTA reads a table after S4, and the next query's tables are
+    // written only after cluster barrier #4, when every remote read of the
+    // histograms is done
+    A.o_rsel = A.o_tab;
+    o = align16(o + std::max<uint64_t>((uint64_t)ix->Ns * A.tab_stride, 4ull * 512));
     A.o_q = (uint32_t)o;
-    o = align16(o + 4ull * ix->ld);
+    A.ldq = (ix->d + 15) & ~15;
+    o = align16(o + 4ull * A.ldq);
     A.o_hist = (uint32_t)o;
     o = align16(o + 4ull * (256 + 64));
     A.o_misc = (uint32_t)o;
     o = align16(o + 4ull * 160);
+
     A.o_cnt = (uint32_t)o;
     o = align16(o + 4ull * NC * (1 + CL + NT / 32));
     // S4's segment list; from S5 on, CTA 0's inbox of the CL local top-k lists
@@ -1493,6 +1696,10 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     A.beta_per = p->beta_per_query;
     A.out_ids = ids;
     A.out_dist = dist;
+    A.precision = p->precision;
+    A.R = (uint32_t)(p->exact_rerank > 0 ? p->exact_rerank : 512);
+    A.Xh = ix->Xh;
+    A.ldh = ix->ldh;
 
     if (dbg) {
         A.dbg_teff = dbg->t_eff;
@@ -1500,6 +1707,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
         A.dbg_dtab = dbg->dtab;
         A.dbg_scores = dbg->scores;
         A.dbg_cands = dbg->cands;
+        A.dbg_surv = dbg->survivors;
     }
     const bool persistent = (p->flags & SUCO_QUERY_ONE_CLUSTER_PER_QUERY) == 0;
     // each call takes the next of the index's work counters in turn

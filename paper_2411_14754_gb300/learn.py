@@ -231,13 +231,13 @@ def query_learned(index: S.SucoIndex, model: Mlp, Qd: torch.Tensor, k: int, offs
                               beta_per_query=beta, **kw)
 
 
-def tune_offsets(index, model, Qd, gt, k, target=0.95, grid=np.arange(-1.0, 2.51, 0.125)):
+def tune_offsets(index, model, Qd, gt, k, target=0.95, grid=np.arange(-1.0, 2.51, 0.125), **kw):
     """Smallest common margin (log space, added to both outputs) whose mean
     recall@k on (Qd, gt) reaches the target; the largest tried if none does.
-    Returns (margin, recall)."""
+    Extra keywords go to the query (e.g. precision).  Returns (margin, recall)."""
     r = 0.0
     for m in grid:
-        ids, _ = query_learned(index, model, Qd, k, offsets=(m, m))
+        ids, _ = query_learned(index, model, Qd, k, offsets=(m, m), **kw)
         r = float(recall_rows(ids.cpu().numpy(), gt).mean())
         if r >= target:
             return float(m), r
