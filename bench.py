@@ -452,6 +452,150 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     pkg.suco_free(index)
 
 
+def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
+    """A stream of queries with per-query k and alpha drawn uniformly from the
+    workload's mixes: one launch per batch through the persistent kernel (each
+    cluster takes the next unanswered query from a work counter), the launch
+    shape picked by the autotuner, each batch's launch captured once in a CUDA
+    graph and replayed in the timed region."""
+    w = W.WORKLOADS[args.workload]
+    X = W.dataset(w.number)
+    Qall = W.queries(w.number)
+    ks, als = W.per_query_mix(w.number, w.nq)
+    kmax = int(max(w.k_mix))
+    Xd = torch.from_numpy(X).to(dev)
+    t0 = time.time()
+    index = pkg.suco_build_index(Xd, w.Ns, w.sqrtK, w.kmeans_iters,
+                                 init_ids=W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK))
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    note(f"index built in {build_s:.1f}s")
+    B = w.batch
+    nb = (w.nq + B - 1) // B
+    sl = [slice(i * B, min(w.nq, (i + 1) * B)) for i in range(nb)]
+    batches = [torch.from_numpy(Qall[c]).to(dev) for c in sl]
+    kq = [torch.from_numpy(ks[c].astype(np.int32)).to(dev) for c in sl]
+    aq = [torch.from_numpy(als[c].astype(np.float32)).to(dev) for c in sl]
+    outs = [(torch.empty((b.shape[0], kmax), dtype=torch.int32, device=dev),
+             torch.empty((b.shape[0], kmax), dtype=torch.float32, device=dev)) for b in batches]
+    order = [(rank + i * world) % nb for i in range(nb)]
+    amax = float(max(w.alpha_mix))
+    shape = pkg.suco_autotune(index, batches[0], kmax, amax, w.beta, k_per_query=kq[0], alpha_per_query=aq[0])
+    note(f"autotuned launch shape (cluster size, threads): {shape}")
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+
+    def launch(bi, st):
+        pkg.suco_query_batch(index, batches[bi], kmax, amax, w.beta, out_ids=outs[bi][0], out_dist=outs[bi][1],
+                             k_per_query=kq[bi], alpha_per_query=aq[bi], stream=st)
+
+    mine = sorted(set(order))
+    with torch.cuda.stream(stream):
+        for bi in mine:
+            launch(bi, stream)  # first call of each shape outside capture
+    torch.cuda.synchronize()
+    graphs = {}
+    for bi in mine:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            launch(bi, stream)
+        graphs[bi] = g
+    torch.cuda.synchronize()
+
+    def step(s, ev):
+        graphs[order[s % nb]].replay()
+
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    nq_step = [batches[order[s % nb]].shape[0] for s in range(args.steps)]
+    with ClockSampler(local_rank) as clk, torch.cuda.stream(stream):
+        total_ms, parts = time_loop(torch, stream, args.steps, args.warmup, step)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    tot = torch.tensor([total_ms, float(sum(nq_step))], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx, sm = tot.clone(), tot.clone()
+        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
+        total_ms, all_q = float(mx[0]), float(sm[1])
+    else:
+        all_q = float(sum(nq_step))
+    value = all_q / (total_ms / 1000.0)
+    mean_launch_ms = total_ms / args.steps
+
+    # end to end: pinned host queries, k and alpha copied into the captured input buffers, graph replay, results back
+    hq = [b.cpu().pin_memory() for b in batches]
+    hk = [t.cpu().pin_memory() for t in kq]
+    ha = [t.cpu().pin_memory() for t in aq]
+    hout = [(torch.empty(o[0].shape, dtype=torch.int32).pin_memory(),
+             torch.empty(o[1].shape, dtype=torch.float32).pin_memory()) for o in outs]
+
+    def e2e_step(s, ev):
+        bi = order[s % nb]
+        batches[bi].copy_(hq[bi], non_blocking=True)
+        kq[bi].copy_(hk[bi], non_blocking=True)
+        aq[bi].copy_(ha[bi], non_blocking=True)
+        graphs[bi].replay()
+        hout[bi][0].copy_(outs[bi][0], non_blocking=True)
+        hout[bi][1].copy_(outs[bi][1], non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        e2e_ms, _ = time_loop(torch, stream, args.steps, args.warmup, e2e_step)
+    h2d = d2h = 0
+    for s in range(args.steps):
+        bi = order[(args.warmup + s) % nb]
+        h2d += hq[bi].numel() * 4 + hk[bi].numel() * 4 + ha[bi].numel() * 4
+        d2h += hout[bi][0].numel() * 4 + hout[bi][1].numel() * 4
+    e2e_value = sum(nq_step) / (e2e_ms / 1000.0)
+
+    # recall@k_b of a sample of queries against exact k-NN, and T_eff for the roofline
+    from paper_2411_14754_gb300 import learn as L
+    ns = min(args.recall_sample, batches[0].shape[0])
+    q0 = batches[0][:ns]
+    gt = L.exact_knn(Xd, q0, kmax, chunk=64)
+    ids0 = outs[0][0][:ns].cpu().numpy()
+    kk = ks[:ns]
+    rec = float(np.mean([len(set(ids0[j, :kk[j]].tolist()) & set(gt[j, :kk[j]].tolist())) / kk[j]
+                         for j in range(ns)]))
+    dbg = pkg.suco_query_debug(index, q0, kmax, amax, w.beta, want=("t_eff",), k_per_query=kq[0][:ns].contiguous(),
+                               alpha_per_query=aq[0][:ns].contiguous())
+    teff = float(dbg["t_eff"].double().sum(dim=1).mean().item())
+    del Xd
+    Cc = pkg.suco_thresholds(w.n, amax, w.beta, kmax)[1]
+    bpq = 4.0 * teff + 4.0 * Cc * w.d
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    peak_src = "measured" if peaks.get("hbm_gbs") else "fallback"
+    achieved = bpq * B / (mean_launch_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": committed_traffic(f"{w.number}-mix"), "peak_source": peak_src,
+                "kernel": "suco_query_kernel (mixed per-query k and alpha, multi-pass over the id range, "
+                          "CUDA-graph replay, one launch per batch)",
+                "algorithmic_bytes_per_query": bpq, "mean_launch_ms": mean_launch_ms}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as _o
+        cpu = run_cpu_baseline(w, X, Qall, _o.max_threads(), alpha=float(np.mean(w.alpha_mix)),
+                               target_s=args.cpu_seconds)
+    if rank == 0:
+        cfg = workload_config(w, B)
+        cfg["workload"] = (f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, beta={w.beta}, per-query k in "
+                           f"{list(w.k_mix)} and alpha in {list(w.alpha_mix)} drawn uniformly, FP32")
+        cfg["launch"] = {"cluster_size": shape[0], "threads": shape[1], "cuda_graphs": True, "persistent": True}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": mean_launch_ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+                "recall_at_k": rec, "recall_note": "mean over a sample of recall@k_b with each query's own k_b",
+                "t_eff_per_query": teff, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                        "d2h_bytes_per_step": d2h // args.steps},
+                "clocks": clk.summary(), "gpu_launches": args.steps, "index_build_s": build_s}
+        print(json.dumps(line), flush=True)
+    pkg.suco_free(index)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -470,6 +614,11 @@ def main():
     dev = torch.device("cuda", local_rank)
     pkg.load_library()
     w = W.WORKLOADS[args.workload]
+    if w.k_mix and not args.plain:
+        run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev)
+        if world > 1:
+            tdist.destroy_process_group()
+        return
     if w.n_train and not args.plain:
         run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev)
         if world > 1:

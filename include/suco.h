@@ -135,6 +135,10 @@ typedef struct suco_query_params {
     const float* beta_per_query;   /* (device, nullable) [nq], clamped to (0, beta]     */
     int32_t precision;    /* SUCO_PRECISION_*; BF16 needs suco_add_reduced_copies      */
     int32_t exact_rerank; /* R: survivors of the coarse pass (0 = 512), up to 2^24       */
+    int32_t id_passes;    /* passes over the id range (0 = automatic: the fewest whose
+                             SC-score counters fit on chip; else a power of two); the
+                             result does not depend on it                            */
+    int32_t reserved0;    /* must be 0                                               */
 } suco_query_params;
 
 /* Answers nq queries (Algorithm 4; Algorithm 3 for the cell walk).
@@ -155,8 +159,8 @@ typedef struct suco_query_debug_out {
     uint8_t* activated;  /* (device) [nq][Ns][K] 1 where the cell was retrieved            */
     float* dtab;         /* (device) [nq][Ns][2][sqrtK] FP32 squared centroid distances    */
     uint8_t* scores;     /* (device) [nq][n] SC-scores (Definition 4)                      */
-    int32_t* cands;      /* (device) [nq][C] candidate ids: the ids scoring above the cut in
-                            ascending id order, then the lowest-id ties at the cut         */
+    int32_t* cands;      /* (device) [nq][C] candidate ids in ascending id order: every id
+                            scoring above the cut and the lowest-id ties at the cut       */
     uint8_t* survivors;  /* (device) [nq][n], zeroed by the caller: set to 1 for every
                             candidate that survives the BF16 coarse pass                    */
 } suco_query_debug_out;

@@ -104,8 +104,9 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
     }
     ix->K = (int64_t)sqrtK * sqrtK;
     ix->ld = (d + 3) & ~3;
-    int64_t nch = (n + NCH - 1) / NCH;
-    ix->n_ch = (nch + 31) & ~int64_t(31);
+    ix->nch = MIN_NCH;
+    while ((n + ix->nch - 1) / ix->nch > MAX_CHUNK) ix->nch *= 2;
+    ix->n_ch = (((n + ix->nch - 1) / ix->nch) + 31) & ~int64_t(31);
     SUCO_CUDA_TRY(cudaGetDevice(&ix->device));
     struct {
         void** p;
@@ -115,7 +116,7 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
         {(void**)&ix->cent, (size_t)Ns * 2 * sqrtK * ix->hmax * 4},
         {(void**)&ix->cell_off, (size_t)Ns * (ix->K + 1) * 4},
         {(void**)&ix->perm, (size_t)Ns * n * 4},
-        {(void**)&ix->split, (size_t)Ns * (NCH + 1) * ix->K * 4},
+        {(void**)&ix->split, (size_t)Ns * (ix->nch + 1) * ix->K * 4},
         {(void**)&ix->work, (size_t)WORK_SLOTS * WORK_STRIDE * 4},
     };
     ix->bytes = 0;
@@ -150,6 +151,8 @@ int check_query_params(const suco_index* index, const float* queries, int64_t nq
         return fail(SUCO_EINVAL, "precision=%d must be SUCO_PRECISION_FP32 or SUCO_PRECISION_BF16", p->precision);
     if (p->precision == SUCO_PRECISION_BF16 && !index->ix.Xh)
         return fail(SUCO_ESTATE, "the index has no BF16 copy: call suco_add_reduced_copies first");
+    if (p->id_passes < 0) return fail(SUCO_EINVAL, "id_passes=%d must not be negative", p->id_passes);
+    if (p->reserved0 != 0) return fail(SUCO_EINVAL, "reserved0 must be 0");
     if (p->exact_rerank < 0 || p->exact_rerank > (1 << 24))
         return fail(SUCO_EINVAL, "exact_rerank=%d must be in [0, 2^24]", p->exact_rerank);
     if (nq > 0 && (!queries || !ids || !dist)) return fail(SUCO_EINVAL, "queries/out_ids/out_dist must not be NULL");

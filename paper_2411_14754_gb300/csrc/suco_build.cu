@@ -192,13 +192,13 @@ __global__ void cell_off_kernel(const uint32_t* __restrict__ sorted_cells, int64
 
 // split[i][j][x] = position (inside perm[i]) of the first id >= j*n_ch in cell x.
 __global__ void split_kernel(const uint32_t* __restrict__ cell_off, const int32_t* __restrict__ perm, int64_t n,
-                             int32_t Ns, int64_t K, int64_t n_ch, uint32_t* __restrict__ split)
+                             int32_t Ns, int64_t K, int64_t n_ch, int32_t nch, uint32_t* __restrict__ split)
 {
-    const int64_t total = (int64_t)Ns * (NCH + 1) * K;
+    const int64_t total = (int64_t)Ns * (nch + 1) * K;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t x = t % K;
-        const int64_t j = (t / K) % (NCH + 1);
-        const int64_t i = t / (K * (NCH + 1));
+        const int64_t j = (t / K) % (nch + 1);
+        const int64_t i = t / (K * (nch + 1));
         const uint32_t* co = cell_off + i * (K + 1);
         const int32_t* pm = perm + i * n;
         int64_t lo = co[x], hi = co[x + 1];
@@ -244,8 +244,8 @@ int build_imi(DeviceIndex* ix, const int32_t* assign, cudaStream_t st)
                                                               ix->cell_off + (int64_t)i * (K + 1));
         SUCO_CUDA_TRY(cudaGetLastError());
     }
-    split_kernel<<<grid_for((int64_t)ix->Ns * (NCH + 1) * K, 256), 256, 0, st>>>(ix->cell_off, ix->perm, n, ix->Ns,
-                                                                                  K, ix->n_ch, ix->split);
+    split_kernel<<<grid_for((int64_t)ix->Ns * (ix->nch + 1) * K, 256), 256, 0, st>>>(
+        ix->cell_off, ix->perm, n, ix->Ns, K, ix->n_ch, ix->nch, ix->split);
     SUCO_CUDA_TRY(cudaGetLastError());
     SUCO_CUDA_TRY(cudaStreamSynchronize(st));
     return SUCO_OK;

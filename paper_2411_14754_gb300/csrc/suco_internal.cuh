@@ -12,13 +12,15 @@
 
 namespace suco {
 
-// The id range [0, n) is cut into NCH equal chunks of n_ch ids (n_ch a
-// multiple of 32).  For every (subspace, cell) the index stores where each
+// The id range [0, n) is cut into nch equal chunks of n_ch ids (n_ch a
+// multiple of 32; nch a power of two, at least MIN_NCH, with chunks of at most
+// MAX_CHUNK ids).  For every (subspace, cell) the index stores where each
 // chunk starts inside the cell's id list, so that a CTA that owns a chunk
 // range reads only its own ids of a cell.
 constexpr int WORK_SLOTS = 64;
 constexpr int WORK_STRIDE = 8;  // 32 bytes per slot
-constexpr int NCH = 16;
+constexpr int MIN_NCH = 64;
+constexpr int64_t MAX_CHUNK = 1 << 17;
 
 struct DeviceIndex {
     int64_t n = 0;
@@ -30,13 +32,14 @@ struct DeviceIndex {
     int64_t K = 0;
     int64_t ld = 0;     // row stride of X in floats (d rounded up to 4)
     int64_t n_ch = 0;   // ids per chunk
+    int32_t nch = 0;    // chunks
     float* X = nullptr;           // [n][ld]; columns d..ld-1 are zero
     uint16_t* Xh = nullptr;       // optional BF16 copy of X, [n][ldh] (ldh = d rounded up to 8), padding zero
     int64_t ldh = 0;
     float* cent = nullptr;        // [Ns][2][sqrtK][hmax]; padding zero
     uint32_t* cell_off = nullptr; // [Ns][K+1] offsets into perm[i]
     int32_t* perm = nullptr;      // [Ns][n] ids grouped by cell, ascending inside a cell
-    uint32_t* split = nullptr;    // [Ns][NCH+1][K] absolute position in perm[i] where chunk j starts in cell x
+    uint32_t* split = nullptr;    // [Ns][nch+1][K] absolute position in perm[i] where chunk j starts in cell x
     // work counters of persistent query launches: WORK_SLOTS pairs (next query,
     // finished clusters), WORK_STRIDE words apart, zero between launches; calls
     // take the slots in turn (work_next), so up to WORK_SLOTS calls on one index

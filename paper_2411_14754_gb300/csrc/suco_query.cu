@@ -88,6 +88,9 @@ struct QArgs {
     uint32_t R;                        // survivors of the coarse pass
     uint8_t* dbg_surv;                 // [nq][n] 1 for the coarse pass's survivors (debug)
     uint32_t o_rsel;                   // [2][256] published radix histograms of the survivor cut
+    uint32_t npass;                    // passes over the id range (S4 + S5 per pass)
+    uint32_t o_run, run_stride;        // running candidate list of a multi-pass query: ids [2][stride], scores [2][stride]
+    int32_t nch;                       // id chunks of the index (rows of split per subspace, minus one)
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -111,8 +114,12 @@ __device__ __forceinline__ uint32_t cluster_rank()
     return r;
 }
 
+// The .aligned barrier must be executed by every thread of a warp together:
+// __syncwarp() reconverges the warp first (the compiler does not know that the
+// inline barrier needs convergence).
 __device__ __forceinline__ void cluster_sync()
 {
+    __syncwarp();
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
@@ -618,7 +625,7 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
             }
             const uint32_t sigma = rl - tb.row_pre[lo];
             const uint32_t cell = (uint32_t)tb.idx1[lo] * (uint32_t)sk + tb.idx2[sigma];
-            const uint32_t* sp = A.split + (int64_t)i * (NCH + 1) * A.K + cell;
+            const uint32_t* sp = A.split + (int64_t)i * (A.nch + 1) * A.K + cell;
             const uint32_t s0 = __ldg(sp + (int64_t)j0 * A.K);
             const uint32_t s1 = __ldg(sp + (int64_t)j1 * A.K);
             len[u] = s1 - s0;
@@ -1055,7 +1062,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         const float* qg = A.Q + b * A.d;
         for (int j = threadIdx.x; j < A.ldq; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
         uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);
-        for (int t = threadIdx.x; t < NC; t += NT) cnt[t] = 0u;
+        for (int t = threadIdx.x; t < 2 * NC; t += NT) cnt[t] = 0u;
     }
     __syncthreads();
 
@@ -1087,9 +1094,13 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     }
     __syncthreads();
 
-    // ---- S4: set the collision bits of this CTA's id range
-    const uint32_t id0 = r * A.span;
-    const int j0 = r * A.cpc, j1 = (r + 1) * A.cpc;
+    // ---- S4 + S5 over the id range in A.npass passes.  In pass p, CTA r owns
+    // the ids of block p*CL + r (A.cpc chunks).  With one pass the cut of S5 is
+    // final.  With several, the cluster keeps a running candidate list, the
+    // first qC entries by (score desc, id asc) among the ids seen so far, in id
+    // order and spread over the CTAs by position (qper each): every pass merges
+    // its ids into it with the same cut.  An id of the final top-qC is in the
+    // top-qC of the ids seen up to its own pass, so nothing it needs is lost.
     uint32_t* sub_pre = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 32;  // [Ns+1]
     if (threadIdx.x == 0) {
         uint32_t acc = 0;
@@ -1099,169 +1110,256 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         }
         sub_pre[A.Ns] = acc;
     }
-    __syncthreads();
+    __syncthreads();  // sub_pre is read by every thread below
     uint32_t* planes = reinterpret_cast<uint32_t*>(smem + A.o_union);  // counters, then [B][G] sliced scores
-    const uint32_t L = sub_pre[A.Ns];
-    for (uint32_t e0 = 0; e0 < L; e0 += MAXSEG)
-        scan_segments<NT>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, sub_wb, planes, id0, j0, j1);
-
-    const uint32_t valid = id0 >= A.n ? 0u : (uint32_t)min((int64_t)A.span, A.n - (int64_t)id0);
-    {
-        // the candidate slots share the (now dead) segment region; other CTAs
-        // fill them after cluster barrier #2
-        uint32_t* sl = reinterpret_cast<uint32_t*>(smem + A.o_slots);
-        for (uint32_t t = threadIdx.x; t < A.per_cta; t += NT) sl[t] = 0xffffffffu;
-    }
-    counters_to_planes<NT, B>(A, planes, (valid + 31) / 32);
-    __syncthreads();
-    if (A.dbg_scores)
-        for (uint32_t j = threadIdx.x; j < valid; j += NT) {
-            uint32_t sc = 0;
-            for (int q = 0; q < B; ++q) sc |= ((planes[(uint32_t)q * A.G + (j >> 5)] >> (j & 31)) & 1u) << q;
-            A.dbg_scores[b * A.n + id0 + j] = (uint8_t)sc;
-        }
-
-    // ---- S5: counts of scores >= s per warp range, the cut theta, hand-off
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);  // this CTA's published counts [NC]
-    uint32_t* allc = cnt + NC;                                     // [CL][NC]
-    uint32_t* wcnt = allc + CL * NC;                               // [NW][NC]
-    const uint32_t ngroups = (valid + 31) / 32;
-    const uint32_t gpw = (ngroups + NW - 1) / NW;
-    const uint32_t gb = min(ngroups, (uint32_t)warp * gpw), ge = min(ngroups, gb + gpw);
-    {
-        uint32_t c[NSMAX];
-#pragma unroll
-        for (int s = 0; s < NSMAX; ++s) c[s] = 0u;
-        for (uint32_t g = gb + lane; g < ge; g += 32) {
-            uint32_t acc[B];
-            load_scores<B>(planes, A.G, g, acc);
-#pragma unroll
-            for (int s = 0; s < NSMAX; ++s)
-                if (s < A.Ns) c[s] += __popc(bitsliced_ge<B>(acc, (uint32_t)(s + 1)));
-        }
-#pragma unroll
-        for (int s = 0; s < NSMAX; ++s) {
-            uint32_t v = c[s];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) {
-                wcnt[warp * NC + s + 1] = v;
-                if (v) atomicAdd(&cnt[s + 1], v);
-            }
-        }
-        if (lane == 0) {
-            const uint32_t lo = gb * 32, hi = min(valid, ge * 32);
-            wcnt[warp * NC] = hi > lo ? hi - lo : 0u;
-            wcnt[warp * NC + NSMAX + 1] = 0u;
-        }
-        if (threadIdx.x == 0) cnt[0] = valid;
-    }
-    cluster_sync();  // #2: every CTA's counts are published
-    uint32_t* sel = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 72;  // theta, n_gt, need_eq
-    uint32_t* slot_base = sel + 8;                                      // [CL] remote slot addresses
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);  // published: [NC] pass counts, [NC] list counts
+    uint32_t* allc = cnt + 2 * NC;                                 // [CL][2][NC]
+    uint32_t* wcnt = allc + 2 * CL * NC;                           // [NW][NC]
+    uint32_t* sel = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 72;  // theta, keep, need_eq, RG, RE, rg_pre, re_pre
+    uint32_t* slot_base = sel + 8;                                      // [CL] remote id-slot addresses
     uint32_t* wbase = reinterpret_cast<uint32_t*>(smem + A.o_hist);     // [NW][2] per-warp output bases
-    for (int t = threadIdx.x; t < CL * NC; t += NT) {
-        const int rr = t / NC, s = t - rr * NC;
-        allc[t] = ld_cluster_u32(map_rank(smem_addr(cnt + s), (uint32_t)rr));
-    }
-    for (int t = threadIdx.x; t < CL; t += NT) slot_base[t] = map_rank(smem_addr(smem + A.o_slots), (uint32_t)t);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int theta = 0;
-        for (int s = A.Ns; s >= 1; --s) {
-            uint32_t tot = 0;
-            for (int rr = 0; rr < CL; ++rr) tot += allc[rr * NC + s];
-            if (tot >= qC) {
-                theta = s;
-                break;
+    const uint32_t L = sub_pre[A.Ns];
+    const bool multi = A.npass > 1;
+    uint32_t run_n = 0;  // entries of the running list (the same in every CTA)
+    uint32_t* ids_out = reinterpret_cast<uint32_t*>(smem + A.o_slots);
+    for (uint32_t pass = 0; pass < A.npass; ++pass) {
+        const uint32_t blk = pass * (uint32_t)CL + r;
+        const uint32_t id0 = blk * A.span;
+        const int j0 = (int)(blk * (uint32_t)A.cpc), j1 = j0 + A.cpc;
+        // list buffers: read [pass & 1], write [(pass + 1) & 1]; one pass writes the S6 slots
+        const uint32_t* ids_in = multi ? reinterpret_cast<const uint32_t*>(smem + A.o_run) + (pass & 1) * A.run_stride
+                                       : nullptr;
+        const uint8_t* sc_in = multi ? reinterpret_cast<const uint8_t*>(smem + A.o_run + 8u * A.run_stride) +
+                                           (pass & 1) * A.run_stride
+                                     : nullptr;
+        ids_out = multi ? reinterpret_cast<uint32_t*>(smem + A.o_run) + ((pass + 1) & 1) * A.run_stride
+                        : reinterpret_cast<uint32_t*>(smem + A.o_slots);
+        uint8_t* sc_out = multi ? reinterpret_cast<uint8_t*>(smem + A.o_run + 8u * A.run_stride) +
+                                      ((pass + 1) & 1) * A.run_stride
+                                : nullptr;
+        if (pass > 0) {
+            uint4* pw = reinterpret_cast<uint4*>(planes);
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            for (uint32_t w = threadIdx.x; w < (A.nstore * A.G + 3) / 4; w += NT) pw[w] = z;
+            for (int t = threadIdx.x; t < 2 * NC; t += NT) cnt[t] = 0u;
+        }
+        __syncthreads();
+        for (uint32_t e0 = 0; e0 < L; e0 += MAXSEG)
+            scan_segments<NT>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, sub_wb, planes, id0, j0, j1);
+
+        const uint32_t valid = id0 >= A.n ? 0u : (uint32_t)min((int64_t)A.span, A.n - (int64_t)id0);
+        if (!multi) {
+            // the candidate slots share the (now dead) segment region; other CTAs
+            // fill them after cluster barrier #2
+            for (uint32_t t = threadIdx.x; t < A.per_cta; t += NT) ids_out[t] = 0xffffffffu;
+        }
+        counters_to_planes<NT, B>(A, planes, (valid + 31) / 32);
+        __syncthreads();
+        if (A.dbg_scores)
+            for (uint32_t j = threadIdx.x; j < valid; j += NT) {
+                uint32_t sc = 0;
+                for (int q = 0; q < B; ++q) sc |= ((planes[(uint32_t)q * A.G + (j >> 5)] >> (j & 31)) & 1u) << q;
+                A.dbg_scores[b * A.n + id0 + j] = (uint8_t)sc;
             }
-        }
-        uint32_t n_gt = 0, gt_pre = 0, eq_pre = 0;
-        for (int rr = 0; rr < CL; ++rr) {
-            const uint32_t* cr = allc + rr * NC;
-            const uint32_t gt = cr[theta + 1];
-            const uint32_t eq = cr[theta] - gt;
-            n_gt += gt;
-            if (rr < (int)r) {
-                gt_pre += gt;
-                eq_pre += eq;
-            }
-        }
-        // per-warp output bases, warps in id order
-        uint32_t sg = gt_pre, se = eq_pre;
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t gt = wcnt[w * NC + theta + 1];
-            const uint32_t eq = wcnt[w * NC + theta] - gt;
-            wbase[2 * w] = sg;
-            wbase[2 * w + 1] = se;
-            sg += gt;
-            se += eq;
-        }
-        sel[0] = (uint32_t)theta;
-        sel[1] = n_gt;
-        sel[2] = qC - n_gt;
-    }
-    __syncthreads();
-    {
-        const uint32_t theta = sel[0], n_gt = sel[1], need_eq = sel[2];
-        uint32_t pgb = wbase[2 * warp], peb = wbase[2 * warp + 1];
-        for (uint32_t g0 = gb; g0 < ge; g0 += 32) {
-            const bool want_eq = peb < need_eq;
-            const uint32_t g = g0 + lane;
-            uint32_t gm = 0, em = 0;
-            if (g < ge) {
+
+        // ---- S5: counts of scores >= s per warp range (this pass's ids) and
+        // per score of the running list's entries; the cut; the hand-off
+        const uint32_t ngroups = (valid + 31) / 32;
+        const uint32_t gpw = (ngroups + NW - 1) / NW;
+        const uint32_t gb = min(ngroups, (uint32_t)warp * gpw), ge = min(ngroups, gb + gpw);
+        {
+            uint32_t c[NSMAX];
+#pragma unroll
+            for (int s = 0; s < NSMAX; ++s) c[s] = 0u;
+            for (uint32_t g = gb + lane; g < ge; g += 32) {
                 uint32_t acc[B];
                 load_scores<B>(planes, A.G, g, acc);
-                gm = bitsliced_ge<B>(acc, theta + 1);
-                em = bitsliced_ge<B>(acc, theta) & ~gm;
-                const uint32_t base = g * 32;
-                if (base + 32 > valid) em &= valid > base ? (0xffffffffu >> (32 - (valid - base))) : 0u;
-            }
-            const uint32_t cg = __popc(gm), ce = __popc(em);
-            const uint32_t any = __ballot_sync(0xffffffffu, (gm | (want_eq ? em : 0u)) != 0u);
-            if (!any) {
-                if (want_eq) peb += __reduce_add_sync(0xffffffffu, ce);
-                continue;
-            }
-            uint32_t ig = cg, ie = ce;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t yg = __shfl_up_sync(0xffffffffu, ig, o);
-                const uint32_t ye = __shfl_up_sync(0xffffffffu, ie, o);
-                if (lane >= o) {
-                    ig += yg;
-                    ie += ye;
+                for (int s = 0; s < NSMAX; ++s)
+                    if (s < A.Ns) c[s] += __popc(bitsliced_ge<B>(acc, (uint32_t)(s + 1)));
+            }
+#pragma unroll
+            for (int s = 0; s < NSMAX; ++s) {
+                uint32_t v = c[s];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) {
+                    wcnt[warp * NC + s + 1] = v;
+                    if (v) atomicAdd(&cnt[s + 1], v);
                 }
             }
-            uint32_t pg = pgb + ig - cg, pe = peb + ie - ce;
-            const uint32_t base_id = id0 + g * 32;
-            while (gm | em) {
-                const int j = __ffs(gm | em) - 1;
-                const uint32_t bit = 1u << j;
-                uint32_t pos = 0xffffffffu;
-                if (gm & bit) {
-                    pos = pg++;
-                } else {
-                    if (pe < need_eq) pos = n_gt + pe;
-                    ++pe;
-                }
-                gm &= ~bit;
-                em &= ~bit;
-                if (pos != 0xffffffffu) {
-                    const uint32_t owner = pos / qper;
-                    const uint32_t id = base_id + (uint32_t)j;
-                    st_cluster_u32(slot_base[owner] + 4u * (pos - owner * qper), id);
-                    if (A.dbg_cands) A.dbg_cands[b * A.C + pos] = (int32_t)id;
-                }
+            if (lane == 0) {
+                const uint32_t lo = gb * 32, hi = min(valid, ge * 32);
+                wcnt[warp * NC] = hi > lo ? hi - lo : 0u;
+                wcnt[warp * NC + NSMAX + 1] = 0u;
             }
-            pgb += __shfl_sync(0xffffffffu, ig, 31);
-            peb += __shfl_sync(0xffffffffu, ie, 31);
+            if (threadIdx.x == 0) cnt[0] = valid;
         }
+        const uint32_t mr = run_n > r * qper ? min(qper, run_n - r * qper) : 0u;  // my list entries
+        if (multi) {
+            uint32_t* rc = cnt + NC;  // [s] = my list entries with score exactly s, then made cumulative
+            for (uint32_t t = threadIdx.x; t < mr; t += NT) atomicAdd(&rc[sc_in[t]], 1u);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t acc = 0;
+                for (int s = NC - 1; s >= 0; --s) {
+                    acc += rc[s];
+                    rc[s] = acc;
+                }
+            }
+        }
+        cluster_sync();  // #2: every CTA's counts are published
+        for (int t = threadIdx.x; t < CL * 2 * NC; t += NT) {
+            const int rr = t / (2 * NC), s = t - rr * 2 * NC;
+            allc[t] = ld_cluster_u32(map_rank(smem_addr(cnt + s), (uint32_t)rr));
+        }
+        for (int t = threadIdx.x; t < CL; t += NT) slot_base[t] = map_rank(smem_addr(ids_out), (uint32_t)t);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // the cut over the list entries and this pass's ids together
+            uint32_t total = 0;
+            for (int rr = 0; rr < CL; ++rr) total += allc[rr * 2 * NC] + allc[rr * 2 * NC + NC];
+            const uint32_t keep = min(qC, total);
+            int theta = 0;
+            for (int s = A.Ns; s >= 1; --s) {
+                uint32_t tot = 0;
+                for (int rr = 0; rr < CL; ++rr) tot += allc[rr * 2 * NC + s] + allc[rr * 2 * NC + NC + s];
+                if (tot >= keep) {
+                    theta = s;
+                    break;
+                }
+            }
+            // output order: the list entries (CTA order), then this pass's ids (CTA order = id order)
+            uint32_t RG = 0, RE = 0, rg_pre = 0, re_pre = 0, PG = 0, pg_pre = 0, pe_pre = 0;
+            for (int rr = 0; rr < CL; ++rr) {
+                const uint32_t* cp = allc + rr * 2 * NC;
+                const uint32_t* cr = cp + NC;
+                const uint32_t rgt = cr[theta + 1], req = cr[theta] - rgt;
+                const uint32_t pgt = cp[theta + 1], peq = cp[theta] - pgt;
+                if (rr < (int)r) {
+                    rg_pre += rgt;
+                    re_pre += req;
+                    pg_pre += pgt;
+                    pe_pre += peq;
+                }
+                RG += rgt;
+                RE += req;
+                PG += pgt;
+            }
+            // per-warp bases of this pass's ids: entries of the output order before the warp's range
+            uint32_t sg = RG + pg_pre, se = RE + pe_pre;
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t gt = wcnt[w * NC + theta + 1];
+                const uint32_t eq = wcnt[w * NC + theta] - gt;
+                wbase[2 * w] = sg;
+                wbase[2 * w + 1] = se;
+                sg += gt;
+                se += eq;
+            }
+            sel[0] = (uint32_t)theta;
+            sel[1] = keep;
+            sel[2] = keep - (RG + PG);  // entries scoring exactly theta that are kept (the lowest ids)
+            sel[3] = rg_pre;
+            sel[4] = re_pre;
+        }
+        __syncthreads();
+        const uint32_t theta = sel[0], keep = sel[1], need_eq = sel[2];
+        if (multi) {
+            // this CTA's list entries, in position order: kept ones move to
+            // position G_before + E_before of the new list
+            uint32_t gcar = sel[3], ecar = sel[4];
+            uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
+            for (uint32_t t0 = 0; t0 < mr; t0 += NT) {
+                const uint32_t t = t0 + threadIdx.x;
+                const uint32_t sc = t < mr ? sc_in[t] : 0u;
+                const uint32_t isg = t < mr && sc > theta, ise = t < mr && sc == theta;
+                uint32_t tot;
+                const uint32_t ex = block_exclusive_scan<NT>((isg << 16) | ise, wtmp, &tot);
+                const uint32_t gb4 = gcar + (ex >> 16), eb4 = ecar + (ex & 0xffffu);
+                if (isg || (ise && eb4 < need_eq)) {
+                    const uint32_t pos = gb4 + min(eb4, need_eq);
+                    const uint32_t owner = pos / qper, sl = pos - owner * qper;
+                    st_cluster_u32(slot_base[owner] + 4u * sl, ids_in[t]);
+                    const uint32_t sa = map_rank(smem_addr(sc_out + sl), owner);
+                    asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(sa), "r"(sc) : "memory");
+                }
+                gcar += tot >> 16;
+                ecar += tot & 0xffffu;
+            }
+        }
+        {
+            uint32_t pgb = wbase[2 * warp], peb = wbase[2 * warp + 1];
+            for (uint32_t g0 = gb; g0 < ge; g0 += 32) {
+                const bool want_eq = peb < need_eq;
+                const uint32_t g = g0 + lane;
+                uint32_t gm = 0, em = 0;
+                uint32_t acc[B];
+#pragma unroll
+                for (int q = 0; q < B; ++q) acc[q] = 0u;
+                if (g < ge) {
+                    load_scores<B>(planes, A.G, g, acc);
+                    gm = bitsliced_ge<B>(acc, theta + 1);
+                    em = bitsliced_ge<B>(acc, theta) & ~gm;
+                    const uint32_t base = g * 32;
+                    if (base + 32 > valid) em &= valid > base ? (0xffffffffu >> (32 - (valid - base))) : 0u;
+                }
+                const uint32_t cg = __popc(gm), ce = __popc(em);
+                const uint32_t any = __ballot_sync(0xffffffffu, (gm | (want_eq ? em : 0u)) != 0u);
+                if (!any) {
+                    if (want_eq) peb += __reduce_add_sync(0xffffffffu, ce);
+                    continue;
+                }
+                uint32_t ig = cg, ie = ce;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t yg = __shfl_up_sync(0xffffffffu, ig, o);
+                    const uint32_t ye = __shfl_up_sync(0xffffffffu, ie, o);
+                    if (lane >= o) {
+                        ig += yg;
+                        ie += ye;
+                    }
+                }
+                uint32_t pg = pgb + ig - cg, pe = peb + ie - ce;
+                const uint32_t base_id = id0 + g * 32;
+                while (gm | em) {
+                    const int j = __ffs(gm | em) - 1;
+                    const uint32_t bit = 1u << j;
+                    uint32_t pos = 0xffffffffu;
+                    if (gm & bit) {
+                        pos = pg + min(pe, need_eq);
+                        ++pg;
+                    } else {
+                        if (pe < need_eq) pos = pg + pe;
+                        ++pe;
+                    }
+                    gm &= ~bit;
+                    em &= ~bit;
+                    if (pos != 0xffffffffu) {
+                        const uint32_t owner = pos / qper, sl = pos - owner * qper;
+                        st_cluster_u32(slot_base[owner] + 4u * sl, base_id + (uint32_t)j);
+                        if (multi) {
+                            uint32_t sc = 0;
+#pragma unroll
+                            for (int q = 0; q < B; ++q) sc |= ((acc[q] >> j) & 1u) << q;
+                            const uint32_t sa = map_rank(smem_addr(sc_out + sl), owner);
+                            asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(sa), "r"(sc) : "memory");
+                        }
+                    }
+                }
+                pgb += __shfl_sync(0xffffffffu, ig, 31);
+                peb += __shfl_sync(0xffffffffu, ie, 31);
+            }
+        }
+        cluster_sync();  // #3: the new list (or, after one pass, every candidate slot) is filled
+        run_n = keep;
     }
-    cluster_sync();  // #3: every candidate slot is filled; the bit planes are dead
+    if (A.dbg_cands) {
+        const uint32_t mc = qC > r * qper ? min(qper, qC - r * qper) : 0u;
+        for (uint32_t t = threadIdx.x; t < mc; t += NT) A.dbg_cands[b * A.C + r * qper + t] = (int32_t)ids_out[t];
+    }
 
     // ---- S6: exact FP32 re-rank of this CTA's share of the candidates
-    const uint32_t* slots = reinterpret_cast<const uint32_t*>(smem + A.o_slots);
+    const uint32_t* slots = ids_out;
     const uint32_t mine = qC > r * qper ? min(qper, qC - r * qper) : 0u;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + A.o_keys);  // [sortP]
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
@@ -1497,12 +1595,14 @@ struct Layout {
     size_t smem = 0;
 };
 
-int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, int k, Layout* L)
+int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uint32_t C, int k, Layout* L)
 {
     QArgs& A = L->A;
     memset(&A, 0, sizeof(A));
     A.CL = CL;
-    A.cpc = NCH / CL;
+    A.npass = (uint32_t)npass;
+    A.nch = ix->nch;
+    A.cpc = ix->nch / (CL * npass);
     A.k = k;
     A.k_pad = (k + 1) & ~1;
     A.per_cta = (C + CL - 1) / CL;
@@ -1528,12 +1628,17 @@ int make_layout(const DeviceIndex* ix, int CL, int nsmax, int NT, uint32_t C, in
     o = align16(o + 4ull * 160);
 
     A.o_cnt = (uint32_t)o;
-    o = align16(o + 4ull * NC * (1 + CL + NT / 32));
+    o = align16(o + 4ull * NC * (2 + 2 * CL + NT / 32));
     // S4's segment list; from S5 on, CTA 0's inbox of the CL local top-k lists
     // followed by this CTA's candidate slots
     A.o_seg = (uint32_t)o;
     A.o_slots = (uint32_t)(o + align16(8ull * CL * k));
     o = align16(o + std::max<uint64_t>(8ull * MAXSEG + 4ull * (MAXSEG + 1), align16(8ull * CL * k) + 4ull * A.per_cta));
+    // a multi-pass query's running candidate list lives across the passes'
+    // S4 (which reuses the segment region), so it has a region of its own
+    A.run_stride = (A.per_cta + 15) & ~15u;
+    A.o_run = (uint32_t)o;
+    if (npass > 1) o = align16(o + 10ull * A.run_stride);
     A.sortP = next_pow2(std::max<uint32_t>(A.per_cta, 1));
     A.o_union = (uint32_t)o;
     A.nbits = nsmax == 8 ? 4 : (nsmax == 16 ? 5 : 6);
@@ -1644,31 +1749,38 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     SUCO_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ix->device));
     // two 512-thread CTAs per SM let the phases of two queries overlap
     const size_t two_per_sm = (size_t)sm_smem / 2 - (size_t)reserved;
+    const int NP = p->id_passes;
+    if (NP < 0 || (NP & (NP - 1)) != 0 || NP > ix->nch)
+        return fail(SUCO_EINVAL, "id_passes=%d must be 0 or a power of two <= %d", NP, ix->nch);
+    // the first shape that fits, in this order: two 512-thread CTAs per SM with
+    // the fewest passes and the smallest cluster, then one 1024-thread CTA per SM
     Layout L;
     bool chosen = false;
-    for (int cl = CL ? CL : 1; cl <= (CL ? CL : 16) && !chosen; cl *= 2) {
-        if (NT == 0 || NT == 512) {
-            make_layout(ix, cl, nsmax, 512, (uint32_t)C, p->k, &L);
-            if (L.smem <= two_per_sm || (NT == 512 && L.smem <= (size_t)dev_smem)) {
-                CL = cl;
-                NT = 512;
-                chosen = true;
+    int npass = 1;
+    for (int stage = 0; stage < 2 && !chosen; ++stage) {
+        const int nt = stage == 0 ? 512 : (NT ? NT : 1024);
+        if (stage == 0 && NT != 0 && NT != 512) continue;
+        for (int np = NP ? NP : 1; np <= (NP ? NP : ix->nch) && !chosen; np *= 2) {
+            for (int cl = CL ? CL : 1; cl <= (CL ? CL : 16) && !chosen; cl *= 2) {
+                if (cl * np > ix->nch) continue;
+                make_layout(ix, cl, np, nsmax, nt, (uint32_t)C, p->k, &L);
+                const bool fits = stage == 0 ? (L.smem <= two_per_sm || (NT == 512 && L.smem <= (size_t)dev_smem))
+                                             : L.smem <= (size_t)dev_smem;
+                if (fits) {
+                    CL = cl;
+                    NT = nt;
+                    npass = np;
+                    chosen = true;
+                }
             }
-        }
-    }
-    for (int cl = CL ? CL : 1; cl <= (CL ? CL : 16) && !chosen; cl *= 2) {
-        const int nt = NT ? NT : 1024;
-        make_layout(ix, cl, nsmax, nt, (uint32_t)C, p->k, &L);
-        if (L.smem <= (size_t)dev_smem) {
-            CL = cl;
-            NT = nt;
-            chosen = true;
         }
     }
     if (!chosen)
         return fail(SUCO_EUNSUPPORTED,
-                    "n=%lld with Ns=%d, C=%lld does not fit the shared memory of %s CTAs (SC-score planes too large)",
-                    (long long)ix->n, ix->Ns, (long long)C, p->cluster_size ? "the requested" : "up to 16");
+                    "n=%lld with Ns=%d, C=%lld does not fit the shared memory of %s CTAs in up to %d passes",
+                    (long long)ix->n, ix->Ns, (long long)C, p->cluster_size ? "the requested" : "up to 16",
+                    NP ? NP : ix->nch);
+    (void)npass;
     if (nq * CL > 0x7fffffffLL) return fail(SUCO_EINVAL, "too many queries in one call");
     QArgs& A = L.A;
     A.X = ix->X;

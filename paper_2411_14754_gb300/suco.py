@@ -31,7 +31,7 @@ class _QueryParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("cluster_size", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
                 ("threads", C.c_int32), ("flags", C.c_int32), ("k_per_query", C.c_void_p),
                 ("alpha_per_query", C.c_void_p), ("beta_per_query", C.c_void_p), ("precision", C.c_int32),
-                ("exact_rerank", C.c_int32)]
+                ("exact_rerank", C.c_int32), ("id_passes", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class _DebugOut(C.Structure):
@@ -180,12 +180,13 @@ COPY_BF16 = 1
 
 
 def _qparams(k, alpha, beta, cluster_size, threads, nq=0, k_per_query=None, alpha_per_query=None,
-             beta_per_query=None, flags=0, precision="fp32", exact_rerank=0):
+             beta_per_query=None, flags=0, precision="fp32", exact_rerank=0, id_passes=0):
     return _QueryParams(int(k), int(cluster_size), float(alpha), float(beta), int(threads), int(flags),
                         _per_query(k_per_query, torch.int32, nq, "k_per_query"),
                         _per_query(alpha_per_query, torch.float32, nq, "alpha_per_query"),
                         _per_query(beta_per_query, torch.float32, nq, "beta_per_query"),
-                        PRECISION[precision] if isinstance(precision, str) else int(precision), int(exact_rerank))
+                        PRECISION[precision] if isinstance(precision, str) else int(precision), int(exact_rerank),
+                        int(id_passes), 0)
 
 
 def suco_add_reduced_copies(index: "SucoIndex", bf16: bool = True, stream=None):
@@ -196,7 +197,8 @@ def suco_add_reduced_copies(index: "SucoIndex", bf16: bool = True, stream=None):
 def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
                      out_ids: Optional[torch.Tensor] = None, out_dist: Optional[torch.Tensor] = None,
                      cluster_size: int = 0, threads: int = 0, stream=None, k_per_query=None, alpha_per_query=None,
-                     beta_per_query=None, flags: int = 0, precision="fp32", exact_rerank: int = 0):
+                     beta_per_query=None, flags: int = 0, precision="fp32", exact_rerank: int = 0,
+                     id_passes: int = 0):
     """Algorithm 4 for every row of ``queries``; returns (ids int32 [nq,k], squared dists float32 [nq,k]).
     Optional per-query CUDA tensors: k_per_query (int32), alpha_per_query, beta_per_query (float32).
     precision "bf16" re-ranks a coarse BF16 pass's exact_rerank survivors (0 = 512) exactly."""
@@ -207,7 +209,7 @@ def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
     p = _qparams(k, alpha, beta, cluster_size, threads, nq, k_per_query, alpha_per_query, beta_per_query, flags,
-                 precision, exact_rerank)
+                 precision, exact_rerank, id_passes)
     _check(load_library().suco_query_batch(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out_ids),
                                            _ptr(out_dist), _stream(stream)))
     return out_ids, out_dist
@@ -216,7 +218,7 @@ def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
 def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
                      cluster_size: int = 0, threads: int = 0, want=("t_eff", "activated", "dtab", "scores", "cands"),
                      stream=None, k_per_query=None, alpha_per_query=None, beta_per_query=None, flags: int = 0,
-                     precision="fp32", exact_rerank: int = 0):
+                     precision="fp32", exact_rerank: int = 0, id_passes: int = 0):
     """suco_query_batch plus per-stage outputs; returns a dict of CUDA tensors."""
     _dev_f32(queries, "queries")
     nq = queries.shape[0]
@@ -234,7 +236,7 @@ def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
     dbg = _DebugOut(*[(out[n].data_ptr() if n in out else None) for n in ("t_eff", "activated", "dtab", "scores",
                                                                         "cands", "survivors")])
     p = _qparams(k, alpha, beta, cluster_size, threads, nq, k_per_query, alpha_per_query, beta_per_query, flags,
-                 precision, exact_rerank)
+                 precision, exact_rerank, id_passes)
     _check(load_library().suco_query_debug(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out["ids"]),
                                            _ptr(out["dist"]), C.byref(dbg), _stream(stream)))
     out["T"], out["C"] = T, Cc

@@ -69,3 +69,40 @@ def test_full_batch_properties(full):
     rows = np.arange(0, len(Q), 7)
     for b in rows:
         np.testing.assert_array_equal(dist[b].astype(np.float64), true_sqdist(X, Q[b], ids[b]))
+
+
+@pytest.fixture(scope="module")
+def large():
+    """4,000,000 points, d=16: the SC-score counters of one query (4 bits per
+    id) no longer fit one pass of a 16-CTA cluster at two CTAs per SM, so the
+    automatic launch takes several passes over the id range."""
+    from paper_2411_14754_gb300 import build
+    build.build()
+    n, d, Ns, sk = 4_000_000, 16, 4, 20
+    rng = np.random.default_rng(77)
+    centres = rng.uniform(0, 100, size=(500, d))
+    X = (centres[rng.integers(0, 500, size=n)] + rng.normal(0, 3.0, size=(n, d))).astype(np.float32)
+    Q = (centres[rng.integers(0, 500, size=256)] + rng.normal(0, 3.0, size=(256, d))).astype(np.float32)
+    idx = oracle.build_index(X, Ns, sk, 1, W.random_init_ids(78, n, Ns, sk))
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).cuda(), Ns, sk, idx["centroids"], idx["assign"])
+    yield X, Q, idx, ix
+    pkg.suco_free(ix)
+
+
+def test_large_index_in_several_passes_sampled_stage_parity(large):
+    X, Q, idx, ix = large
+    k, alpha, beta = 10, 0.02, 0.002
+    Qd = torch.from_numpy(Q).cuda()
+    ids, dist = pkg.suco_query_batch(ix, Qd, k, alpha, beta)
+    torch.cuda.synchronize()
+    sample = [0, 77, 255]
+    dbg = pkg.suco_query_debug(ix, Qd[sample], k, alpha, beta, want=("t_eff", "scores", "cands"))
+    torch.cuda.synchronize()
+    host = {kk: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for kk, v in dbg.items()}
+    for j, b in enumerate(sample):
+        check_query_against_oracle(X, idx, Q[b], host, j, k, host["T"], host["C"])
+        assert ids[b].cpu().tolist() == host["ids"][j].tolist()
+    # the same answer from an explicit single pass on 1024-thread CTAs
+    one = pkg.suco_query_batch(ix, Qd, k, alpha, beta, id_passes=1, threads=1024, cluster_size=16)
+    torch.cuda.synchronize()
+    assert torch.equal(one[0], ids) and torch.equal(one[1], dist)

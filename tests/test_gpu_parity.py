@@ -25,7 +25,8 @@ def built():
     pkg.load_library()
 
 
-def run(X, idx_o, Q, k, alpha, beta, cluster_size=0, threads=0, stages=True, want=None, sample=None, flags=0):
+def run(X, idx_o, Q, k, alpha, beta, cluster_size=0, threads=0, stages=True, want=None, sample=None, flags=0,
+        id_passes=0):
     dev = torch.device("cuda")
     Xd = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
     Qd = torch.from_numpy(np.ascontiguousarray(Q)).to(dev)
@@ -33,7 +34,7 @@ def run(X, idx_o, Q, k, alpha, beta, cluster_size=0, threads=0, stages=True, wan
     try:
         want = want or (("t_eff", "activated", "dtab", "scores", "cands") if stages else ())
         out = pkg.suco_query_debug(ix, Qd, k, alpha, beta, cluster_size=cluster_size, threads=threads, want=want,
-                                   flags=flags)
+                                   flags=flags, id_passes=id_passes)
         torch.cuda.synchronize()
         host = {kk: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for kk, v in out.items()}
     finally:
@@ -186,16 +187,23 @@ def test_argument_errors_on_device(tiny):
 
 
 def test_score_array_too_large_is_reported():
-    # the sliced SC-score planes (bits(Ns)+1 bits per id) must fit in the shared
-    # memory of at most 16 CTAs: 8M ids x 7 bits is beyond that
+    # forced into one pass, the SC-score counters of 8M ids (Ns = 32: two nibble
+    # sets and two one-bit planes, 10 bits per id) do not fit 16 CTAs
     n = 8_000_000
     dev = torch.device("cuda")
     X = torch.zeros((n, 64), device=dev)
     ix = pkg.suco_build_index(X, 32, 1, 0)
     del X
+    q = torch.zeros((1, 64), device=dev)
     with pytest.raises(pkg.SucoError) as e:
-        pkg.suco_query_batch(ix, torch.zeros((1, 64), device=dev), 10, 0.01, 0.001)
+        pkg.suco_query_batch(ix, q, 10, 0.01, 0.001, id_passes=1)
     assert e.value.code == -6
+    # the automatic launch takes several passes: every point sits on the query
+    # and scores Ns, so the answer is the 10 lowest ids at distance 0
+    ids, dist = pkg.suco_query_batch(ix, q, 10, 0.01, 0.001)
+    torch.cuda.synchronize()
+    assert ids.cpu().tolist() == [list(range(10))]
+    assert dist.abs().max().item() == 0.0
     pkg.suco_free(ix)
 
 
@@ -330,3 +338,39 @@ def test_work_counter_answers_every_query_once_across_calls_and_replays(tiny):
         torch.cuda.synchronize()
         assert torch.equal(ids, ref[0]) and torch.equal(dist, ref[1])
     pkg.suco_free(ix)
+
+
+@pytest.mark.parametrize("id_passes,cluster_size", [(2, 1), (2, 8), (4, 4), (4, 16), (8, 8), (64, 1), (16, 4)])
+def test_tiny_workload_in_several_id_passes(tiny, id_passes, cluster_size):
+    # the running candidate list of a multi-pass query gives the same stages
+    # and results as one pass: checked against the oracle stage by stage
+    w, X, Q, idx = tiny
+    run(X, idx, Q[:24], w.k, w.alpha, w.beta, cluster_size=cluster_size, id_passes=id_passes)
+
+
+@pytest.mark.parametrize("alpha,beta,k", [(0.01, 0.3, 10), (0.2, 0.05, 64), (1.0, 0.01, 5)])
+def test_several_id_passes_with_ties_at_the_cut(tiny, alpha, beta, k):
+    # small alpha with a large beta leaves many ids at score 0 (cut theta = 0,
+    # ties by id across passes); alpha = 1 gives every id the score Ns
+    w, X, Q, idx = tiny
+    run(X, idx, Q[:12], k, alpha, beta, cluster_size=4, id_passes=8)
+
+
+def test_id_passes_do_not_change_the_answer():
+    X = W.random_data(11, 6000, 40, "int")
+    Q = W.random_data(12, 64, 40, "int")
+    idx = oracle.build_index(X, 5, 9, 3, W.random_init_ids(13, 6000, 5, 9))
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).cuda(), 5, 9, idx["centroids"], idx["assign"])
+    try:
+        Qd = torch.from_numpy(Q).cuda()
+        ref = pkg.suco_query_batch(ix, Qd, 16, 0.1, 0.05)
+        for P, CL in ((2, 2), (4, 16), (32, 2), (64, 1)):
+            got = pkg.suco_query_batch(ix, Qd, 16, 0.1, 0.05, id_passes=P, cluster_size=CL)
+            torch.cuda.synchronize()
+            assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1]), (P, CL)
+        with pytest.raises(pkg.SucoError):
+            pkg.suco_query_batch(ix, Qd, 16, 0.1, 0.05, id_passes=3)
+        with pytest.raises(pkg.SucoError):
+            pkg.suco_query_batch(ix, Qd, 16, 0.1, 0.05, id_passes=128)
+    finally:
+        pkg.suco_free(ix)
