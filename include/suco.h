@@ -123,6 +123,18 @@ SUCO_API int suco_build_index_from_assignments(const float* data, int64_t n, int
 #define SUCO_PRECISION_FP32 0
 #define SUCO_PRECISION_BF16 1
 
+/* suco_query_params.rank_precision: how the half-subspace centroid distances
+ * that rank the IMI cells (Algorithm 4, then Algorithm 3) are computed.
+ * FP32: sum of squared differences on CUDA cores, in dimension order.
+ * BF16 (not in the paper): query and centroids rounded to BF16, the inner
+ * products on the tensor cores (tcgen05, FP32 accumulation), the distance
+ * |q|^2 - 2<q,c> + |c|^2 with the norms of the rounded vectors summed in FP32.
+ * It runs as one extra launch per RANK_CHUNK (4096) queries that writes the
+ * tables into the index's workspace; calls that use it must not overlap on
+ * the GPU (they share the workspace). */
+#define SUCO_RANK_FP32 0
+#define SUCO_RANK_BF16 1
+
 typedef struct suco_query_params {
     int32_t k;            /* results per query (the maximum if k_per_query), 1..256   */
     int32_t cluster_size; /* CTAs cooperating on one query (1,2,4,8,16); 0 = automatic  */
@@ -138,7 +150,8 @@ typedef struct suco_query_params {
     int32_t id_passes;    /* passes over the id range (0 = automatic: the fewest whose
                              SC-score counters fit on chip; else a power of two); the
                              result does not depend on it                            */
-    int32_t reserved0;    /* must be 0                                               */
+    int32_t rank_precision; /* SUCO_RANK_*: arithmetic of the centroid distances that
+                               rank the cells (BF16 needs suco_add_reduced_copies)    */
 } suco_query_params;
 
 /* Answers nq queries (Algorithm 4; Algorithm 3 for the cell walk).
@@ -176,6 +189,9 @@ SUCO_API int suco_query_debug(const suco_index* index, const float* queries, int
  * device memory; synchronous.  Errors: SUCO_EINVAL (NULL index, unknown bits),
  * SUCO_ENOMEM, SUCO_ECUDA. */
 #define SUCO_COPY_BF16 1
+/* mask bit 1 (SUCO_COPY_RANK_BF16): reserve the workspace of the BF16
+ * tensor-core ranking, 4096 x Ns x 2 x sqrtK FP32 values. */
+#define SUCO_COPY_RANK_BF16 2
 SUCO_API int suco_add_reduced_copies(suco_index* index, int32_t mask, void* stream);
 
 /* Times every launch shape (cluster size x threads per CTA) that fits, on the
@@ -290,6 +306,14 @@ SUCO_API int suco_thresholds(int64_t n, double alpha, double beta, int32_t k, in
  * scale of the sums). */
 SUCO_API int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int32_t dim_off, int32_t dim_len,
                                  int32_t k, int32_t iters, float* centroids, int32_t* assign, void* stream);
+
+/* Reads and clears the index's device status word.  Kernels never spin
+ * without a limit: a wait on the tensor-core ranking's MMA completion gives up
+ * after about one second, sets SUCO_STATUS_WAIT_TIMEOUT here, and the launch
+ * ends with unreliable tables instead of hanging.  0 means every launch since
+ * the last read completed normally.  Synchronises the device. */
+#define SUCO_STATUS_WAIT_TIMEOUT 1u
+SUCO_API int suco_read_status(suco_index* index, uint32_t* status);
 
 /* Releases the index and its device memory.  NULL-safe. */
 SUCO_API void suco_free(suco_index* index);

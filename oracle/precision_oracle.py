@@ -125,3 +125,23 @@ def coarse_rerank(X, Xhat_rows, q, cands, R, k):
     surv = cands[order[:min(int(R), len(cands))]]
     ids, dist = _o.rerank(X, q, surv, k)
     return dict(survivors=surv, coarse=coarse, coarse_order=order, ids=ids, dist=dist)
+
+
+def bf16_centroid_tables(index, q):
+    """Half-subspace squared distances between the BF16-rounded query and the
+    BF16-rounded centroids, in FP64: [Ns][2][sqrtK].  The tensor-core ranking
+    computes the same quantity as |q|^2 - 2<q,c> + |c|^2 in FP32."""
+    Ns, sk = index["Ns"], index["sqrtK"]
+    cent = np.asarray(index["centroids"], dtype=np.float32)
+    d = len(q)
+    qb = bf16_to_f64(round_bf16(np.asarray(q, dtype=np.float32)))
+    out = np.empty((Ns, 2, sk), dtype=np.float64)
+    norms = np.empty((Ns, 2, sk), dtype=np.float64)
+    for i in range(Ns):
+        for h in range(2):
+            off, ln = _o.half_dims(d, Ns, i, h)
+            cb = bf16_to_f64(round_bf16(cent[i, h, :, :ln]))
+            qq = qb[off:off + ln]
+            out[i, h] = ((cb - qq[None, :]) ** 2).sum(axis=1)
+            norms[i, h] = (qq ** 2).sum() + (cb ** 2).sum(axis=1)
+    return out, norms

@@ -430,10 +430,14 @@ ORC_EXPORT void orc_build_index(const float* X, int64_t n, int32_t d, int32_t Ns
  * Optional outputs (NULL to skip): scores [n]; cands [C]; teff [Ns] (ids
  * collided per subspace); activated [Ns][K] (1 = cell retrieved);
  * dtab [Ns][2][sqrtK] (the centroid distances as used for ranking). */
-ORC_EXPORT int orc_query(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, const float* centroids,
-                         const int64_t* cell_off, const int64_t* perm, const float* q, int32_t k, int64_t T,
-                         int64_t C, int32_t rank_precision, int64_t* out_ids, double* out_dist, int32_t* scores_out,
-                         int64_t* cands_out, int64_t* teff_out, uint8_t* activated_out, double* dtab_out)
+/* Algorithm 4 for one query.  dtab_in (nullable, [Ns][2][sqrtK]) supplies the
+ * half-subspace centroid distances instead of computing them (the tables of
+ * a reduced-precision ranking); everything after them is unchanged. */
+static int query_core(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, const float* centroids,
+                      const int64_t* cell_off, const int64_t* perm, const float* q, int32_t k, int64_t T, int64_t C,
+                      int32_t rank_precision, const double* dtab_in, int64_t* out_ids, double* out_dist,
+                      int32_t* scores_out, int64_t* cands_out, int64_t* teff_out, uint8_t* activated_out,
+                      double* dtab_out)
 {
     int32_t hmax = orc_hmax(d, Ns);
     int64_t K = (int64_t)sqrtK * sqrtK;
@@ -452,7 +456,9 @@ ORC_EXPORT int orc_query(const float* X, int64_t n, int32_t d, int32_t Ns, int32
             double* dd = h == 0 ? dists1 : dists2;
             const float* cb = centroids + (size_t)(2 * i + h) * sqrtK * hmax;
             for (int32_t a = 0; a < sqrtK; ++a) {
-                if (rank_precision == 1)
+                if (dtab_in)
+                    dd[a] = dtab_in[((size_t)i * 2 + h) * sqrtK + a];
+                else if (rank_precision == 1)
                     dd[a] = (double)sqdist32(q + off, cb + (size_t)a * hmax, len);
                 else
                     dd[a] = sqdist64(q + off, cb + (size_t)a * hmax, len);
@@ -490,6 +496,27 @@ ORC_EXPORT int orc_query(const float* X, int64_t n, int32_t d, int32_t Ns, int32
     free(csize);
     free(cells);
     return 0;
+}
+
+ORC_EXPORT int orc_query(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, const float* centroids,
+                         const int64_t* cell_off, const int64_t* perm, const float* q, int32_t k, int64_t T,
+                         int64_t C, int32_t rank_precision, int64_t* out_ids, double* out_dist, int32_t* scores_out,
+                         int64_t* cands_out, int64_t* teff_out, uint8_t* activated_out, double* dtab_out)
+{
+    return query_core(X, n, d, Ns, sqrtK, centroids, cell_off, perm, q, k, T, C, rank_precision, NULL, out_ids,
+                      out_dist, scores_out, cands_out, teff_out, activated_out, dtab_out);
+}
+
+/* Algorithm 4 for one query from given centroid-distance tables (the ranking
+ * is then taken in FP32, as rank_precision 1). */
+ORC_EXPORT int orc_query_from_tables(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
+                                     const float* centroids, const int64_t* cell_off, const int64_t* perm,
+                                     const float* q, int32_t k, int64_t T, int64_t C, const double* dtab_in,
+                                     int64_t* out_ids, double* out_dist, int32_t* scores_out, int64_t* cands_out,
+                                     int64_t* teff_out, uint8_t* activated_out)
+{
+    return query_core(X, n, d, Ns, sqrtK, centroids, cell_off, perm, q, k, T, C, 1, dtab_in, out_ids, out_dist,
+                      scores_out, cands_out, teff_out, activated_out, NULL);
 }
 
 /* Algorithm 4 over a batch of nq queries, one query per OpenMP thread. */

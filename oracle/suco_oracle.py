@@ -55,6 +55,9 @@ def lib():
     L.orc_query.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i32, i64, i64, i32,
                             _i64p, _f64p, vp, vp, vp, vp, vp]
     L.orc_query.restype = C.c_int
+    L.orc_query_from_tables.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i32, i64, i64, _f64p,
+                                        _i64p, _f64p, vp, vp, vp, vp]
+    L.orc_query_from_tables.restype = C.c_int
     L.orc_query_batch.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i64, i32, i64, i64,
                                   i32, i32, _i64p, _f64p]
     L.orc_sc_linear.argtypes = [_f32p, i64, i32, i32, _f32p, i32, i64, i64, _i64p, _f64p, vp]
@@ -229,6 +232,24 @@ def query(X, index, q, k, T, C_, rank_precision=1, debug=True):
                     int(C_), rank_precision, oi, od,
                     _ptr(out.get("scores")), _ptr(out.get("cands")), _ptr(out.get("teff")),
                     _ptr(out.get("activated")), _ptr(out.get("dtab")))
+    return out
+
+
+def query_from_tables(X, index, q, k, T, C_, dtab):
+    """Algorithm 4 for one query with the centroid-distance tables given
+    ([Ns][2][sqrtK]); the cell ranking is then taken in FP32 like the kernel's."""
+    X = _f32(X)
+    n, d = X.shape
+    Ns, sk = index["Ns"], index["sqrtK"]
+    K = sk * sk
+    oi = np.empty(k, dtype=np.int64)
+    od = np.empty(k, dtype=np.float64)
+    out = dict(ids=oi, dist=od, scores=np.empty(n, dtype=np.int32), cands=np.empty(C_, dtype=np.int64),
+               teff=np.empty(Ns, dtype=np.int64), activated=np.empty((Ns, K), dtype=np.uint8))
+    tab = np.ascontiguousarray(dtab, dtype=np.float64).reshape(Ns, 2, sk)
+    lib().orc_query_from_tables(X, n, d, Ns, sk, index["centroids"], index["cell_off"], index["perm"], _f32(q), k,
+                                int(T), int(C_), tab, oi, od, _ptr(out["scores"]), _ptr(out["cands"]),
+                                _ptr(out["teff"]), _ptr(out["activated"]))
     return out
 
 

@@ -70,7 +70,9 @@ void free_index_memory(DeviceIndex* ix)
     cudaFree(ix->split);
     cudaFree(ix->work);
     cudaFree(ix->Xh);
+    cudaFree(ix->rank_ws);
     ix->Xh = nullptr;
+    ix->rank_ws = nullptr;
     ix->work = nullptr;
     ix->X = nullptr;
     ix->cent = nullptr;
@@ -117,7 +119,7 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
         {(void**)&ix->cell_off, (size_t)Ns * (ix->K + 1) * 4},
         {(void**)&ix->perm, (size_t)Ns * n * 4},
         {(void**)&ix->split, (size_t)Ns * (ix->nch + 1) * ix->K * 4},
-        {(void**)&ix->work, (size_t)WORK_SLOTS * WORK_STRIDE * 4},
+        {(void**)&ix->work, (size_t)(STATUS_WORD + WORK_STRIDE) * 4},
     };
     ix->bytes = 0;
     for (auto& e : a) {
@@ -152,7 +154,11 @@ int check_query_params(const suco_index* index, const float* queries, int64_t nq
     if (p->precision == SUCO_PRECISION_BF16 && !index->ix.Xh)
         return fail(SUCO_ESTATE, "the index has no BF16 copy: call suco_add_reduced_copies first");
     if (p->id_passes < 0) return fail(SUCO_EINVAL, "id_passes=%d must not be negative", p->id_passes);
-    if (p->reserved0 != 0) return fail(SUCO_EINVAL, "reserved0 must be 0");
+    if (p->rank_precision != SUCO_RANK_FP32 && p->rank_precision != SUCO_RANK_BF16)
+        return fail(SUCO_EINVAL, "rank_precision=%d must be SUCO_RANK_FP32 or SUCO_RANK_BF16", p->rank_precision);
+    if (p->rank_precision == SUCO_RANK_BF16 && !index->ix.rank_ws)
+        return fail(SUCO_ESTATE, "BF16 ranking needs its tables workspace: call suco_add_reduced_copies with "
+                                 "SUCO_COPY_RANK_BF16 first");
     if (p->exact_rerank < 0 || p->exact_rerank > (1 << 24))
         return fail(SUCO_EINVAL, "exact_rerank=%d must be in [0, 2^24]", p->exact_rerank);
     if (nq > 0 && (!queries || !ids || !dist)) return fail(SUCO_EINVAL, "queries/out_ids/out_dist must not be NULL");
@@ -375,6 +381,17 @@ int suco_thresholds(int64_t n, double alpha, double beta, int32_t k, int64_t* T,
     if (!(alpha > 0.0 && alpha <= 1.0) || !(beta > 0.0 && beta <= 1.0) || k < 1)
         return fail(SUCO_EINVAL, "alpha, beta must be in (0, 1] and k >= 1");
     thresholds(n, alpha, beta, k, T, C);
+    return SUCO_OK;
+}
+
+int suco_read_status(suco_index* index, uint32_t* status)
+{
+    clear_error();
+    if (!index || !status) return fail(SUCO_EINVAL, "index and status must not be NULL");
+    uint32_t* word = index->ix.work + STATUS_WORD;
+    SUCO_CUDA_TRY(cudaDeviceSynchronize());
+    SUCO_CUDA_TRY(cudaMemcpy(status, word, 4, cudaMemcpyDeviceToHost));
+    SUCO_CUDA_TRY(cudaMemset(word, 0, 4));
     return SUCO_OK;
 }
 

@@ -20,6 +20,10 @@ namespace suco {
 constexpr int WORK_SLOTS = 64;
 constexpr int WORK_STRIDE = 8;  // 32 bytes per slot
 constexpr int MIN_NCH = 64;
+// device status word after the work counters: bit 0 = a kernel's bounded wait gave up
+constexpr int STATUS_WORD = WORK_SLOTS * WORK_STRIDE;
+// queries per launch pair of the BF16 tensor-core ranking (tables workspace rows)
+constexpr int64_t RANK_CHUNK = 4096;
 constexpr int64_t MAX_CHUNK = 1 << 17;
 
 struct DeviceIndex {
@@ -35,6 +39,7 @@ struct DeviceIndex {
     int32_t nch = 0;    // chunks
     float* X = nullptr;           // [n][ld]; columns d..ld-1 are zero
     uint16_t* Xh = nullptr;       // optional BF16 copy of X, [n][ldh] (ldh = d rounded up to 8), padding zero
+    float* rank_ws = nullptr;     // optional [RANK_CHUNK][Ns][2][sqrtK] centroid-distance tables (BF16 ranking)
     int64_t ldh = 0;
     float* cent = nullptr;        // [Ns][2][sqrtK][hmax]; padding zero
     uint32_t* cell_off = nullptr; // [Ns][K+1] offsets into perm[i]
@@ -85,6 +90,7 @@ struct DevBuf {
 
 int build_imi(DeviceIndex* ix, const int32_t* assign_dev /*[Ns][2][n]*/, cudaStream_t st);
 int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, cudaStream_t st);
+int rank_bf16_tables(const DeviceIndex* ix, const float* Q, int64_t nq, float* D, cudaStream_t st);
 int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_query_params* p, int32_t* ids,
                  float* dist, const suco_query_debug_out* dbg, cudaStream_t st);
 

@@ -1,6 +1,8 @@
 // Reduced-precision copies of the dataset for the coarse re-rank pass (no
 // counterpart in the paper): the BF16 copy holds every value of D rounded to
 // nearest even, rows padded with zeros to a multiple of 8 values (16 bytes).
+// The same call reserves the workspace of the BF16 tensor-core ranking: the
+// centroid-distance tables of up to RANK_CHUNK queries.
 #include <cuda_bf16.h>
 
 #include "suco_internal.cuh"
@@ -42,7 +44,7 @@ extern "C" int suco_add_reduced_copies(suco_index* index, int32_t mask, void* st
 {
     clear_error();
     if (!index) return fail(SUCO_EINVAL, "index is NULL");
-    if (mask & ~SUCO_COPY_BF16) return fail(SUCO_EINVAL, "unknown copy bits 0x%x", mask);
+    if (mask & ~(SUCO_COPY_BF16 | SUCO_COPY_RANK_BF16)) return fail(SUCO_EINVAL, "unknown copy bits 0x%x", mask);
     DeviceIndex* ix = &index->ix;
     cudaStream_t st = (cudaStream_t)stream;
     if ((mask & SUCO_COPY_BF16) && !ix->Xh) {
@@ -57,6 +59,14 @@ extern "C" int suco_add_reduced_copies(suco_index* index, int32_t mask, void* st
         SUCO_CUDA_TRY(cudaStreamSynchronize(st));
         ix->Xh = b.as<uint16_t>();
         ix->ldh = ldh;
+        ix->bytes += (int64_t)b.bytes;
+        b.release();
+    }
+    if ((mask & SUCO_COPY_RANK_BF16) && !ix->rank_ws) {
+        DevBuf b;
+        int rc = b.alloc((size_t)RANK_CHUNK * ix->Ns * 2 * ix->sqrtK * 4);
+        if (rc) return rc;
+        ix->rank_ws = b.as<float>();
         ix->bytes += (int64_t)b.bytes;
         b.release();
     }

@@ -91,6 +91,7 @@ struct QArgs {
     uint32_t npass;                    // passes over the id range (S4 + S5 per pass)
     uint32_t o_run, run_stride;        // running candidate list of a multi-pass query: ids [2][stride], scores [2][stride]
     int32_t nch;                       // id chunks of the index (rows of split per subspace, minus one)
+    const float* dtab_in;              // [nq][Ns][2][sqrtK] centroid distances computed before (BF16 ranking) or null
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -282,6 +283,10 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     for (int t = threadIdx.x; t < 2 * sk; t += NT) {
         const int h = t >= sk;
         const int a = t - h * sk;
+        if (A.dtab_in) {  // tables of the tensor-core ranking
+            (h ? tb.d2 : tb.d1)[a] = A.dtab_in[((b * A.Ns + i) * 2 + h) * sk + a];
+            continue;
+        }
         const int off = soff + (h ? first : 0);
         const int len = h ? slen - first : first;
         float acc = 0.f;
@@ -1822,6 +1827,44 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
         A.dbg_surv = dbg->survivors;
     }
     const bool persistent = (p->flags & SUCO_QUERY_ONE_CLUSTER_PER_QUERY) == 0;
+    if (p->rank_precision == SUCO_RANK_BF16) {
+        // one tensor-core table launch and one query launch per RANK_CHUNK queries
+        const QArgs base = A;
+        for (int64_t c0 = 0; c0 < nq; c0 += RANK_CHUNK) {
+            const int64_t cnt = std::min<int64_t>(RANK_CHUNK, nq - c0);
+            int rc = rank_bf16_tables(ix, Q + c0 * ix->d, cnt, ix->rank_ws, st);
+            if (rc) return rc;
+            QArgs& C2 = L.A;
+            C2 = base;
+            C2.Q = base.Q + c0 * ix->d;
+            C2.nq = cnt;
+            C2.dtab_in = ix->rank_ws;
+            C2.out_ids = base.out_ids + c0 * base.k;
+            C2.out_dist = base.out_dist + c0 * base.k;
+            if (base.k_per) C2.k_per = base.k_per + c0;
+            if (base.alpha_per) C2.alpha_per = base.alpha_per + c0;
+            if (base.beta_per) C2.beta_per = base.beta_per + c0;
+            if (base.dbg_teff) C2.dbg_teff = base.dbg_teff + c0 * base.Ns;
+            if (base.dbg_act) C2.dbg_act = base.dbg_act + c0 * base.Ns * (int64_t)base.K;
+            if (base.dbg_dtab) C2.dbg_dtab = base.dbg_dtab + c0 * base.Ns * 2 * base.sqrtK;
+            if (base.dbg_scores) C2.dbg_scores = base.dbg_scores + c0 * base.n;
+            if (base.dbg_cands) C2.dbg_cands = base.dbg_cands + c0 * (int64_t)base.C;
+            if (base.dbg_surv) C2.dbg_surv = base.dbg_surv + c0 * base.n;
+            uint32_t* work = ix->work + (size_t)WORK_STRIDE * (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next,
+                                                                                1u, __ATOMIC_RELAXED) % WORK_SLOTS);
+            if (NT == 1024) {
+                if (nsmax == 8) rc = launch_t<1024, 8>(L, cnt, persistent, work, st);
+                else if (nsmax == 16) rc = launch_t<1024, 16>(L, cnt, persistent, work, st);
+                else rc = launch_t<1024, 32>(L, cnt, persistent, work, st);
+            } else {
+                if (nsmax == 8) rc = launch_t<512, 8>(L, cnt, persistent, work, st);
+                else if (nsmax == 16) rc = launch_t<512, 16>(L, cnt, persistent, work, st);
+                else rc = launch_t<512, 32>(L, cnt, persistent, work, st);
+            }
+            if (rc) return rc;
+        }
+        return SUCO_OK;
+    }
     // each call takes the next of the index's work counters in turn
     uint32_t* work = ix->work + (size_t)WORK_STRIDE *
                                     (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next, 1u,

@@ -1,0 +1,228 @@
+// Half-subspace centroid distances of a batch of queries on the 5th-generation
+// tensor cores (the BF16 ranking mode; the paper computes these distances
+// directly, Section 4.2, Algorithm 4, in full precision).
+//
+// For every half-subspace h (length L <= hmax) the block of queries Q_h
+// (128 x L) and the codebook C_h (sqrtK x L) are rounded to BF16 and
+//     D[b][h][c] = |q_bh|^2 - 2 <q_bh, c_hc> + |c_hc|^2
+// with the inner products from tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in
+// tensor memory) and the squared norms of the rounded vectors summed in FP32.
+//
+// One CTA of 128 threads handles 128 queries and every half-subspace in turn:
+// the threads stage both operands in shared memory in the canonical K-major
+// layout without swizzle (core matrices of 8 rows x 16 bytes), one thread
+// issues the MMAs into a 128-lane x NP-column FP32 accumulator, a commit
+// arrives on an mbarrier, and each warp reads its 32 lanes back with
+// tcgen05.ld (one query row per thread).
+#include <cuda_bf16.h>
+
+#include "suco_internal.cuh"
+
+namespace suco {
+namespace {
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor (tcgen05): start address, leading and stride
+// byte offsets (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;
+    return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t instr_desc_bf16(uint32_t m, uint32_t n)
+{
+    return (1u << 4)            // D format F32
+           | (1u << 7)          // A format BF16
+           | (1u << 10)         // B format BF16
+           | ((n >> 3) << 17)   // N / 8
+           | ((m >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// waits at most ~1 s for the phase; false if it gave up
+__device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+constexpr int TC_M = 128;
+
+// dynamic shared memory: A [128 x KP] bf16, B [NP x KP] bf16, |c|^2 [NP] f32,
+// mbarrier (8 B), TMEM address (4 B)
+__global__ void __launch_bounds__(128, 1)
+    centroid_dist_tc_kernel(const float* __restrict__ Q, int64_t nq, int32_t d, int32_t Ns, int32_t sub_s,
+                            int32_t sqrtK, int32_t hmax, const float* __restrict__ cent, int32_t KP, int32_t NP,
+                            int32_t ncols, float* __restrict__ D, uint32_t* status)
+{
+    extern __shared__ __align__(128) char smem[];
+    uint16_t* As = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* Bs = As + TC_M * KP;
+    float* cn = reinterpret_cast<float*>(Bs + NP * KP);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(cn + NP);
+    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t b0 = (int64_t)blockIdx.x * TC_M;
+    const int kcols = KP / 8;  // core-matrix columns along K
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(taddr_s)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *taddr_s;
+    // byte offsets between core matrices: along K (the descriptor's leading
+    // byte offset) and along M or N (its stride byte offset)
+    const uint32_t k_step = 128u, mn_step = (uint32_t)kcols * 128u;
+    const uint32_t lbo = k_step, sbo = mn_step;
+    const uint32_t idesc = instr_desc_bf16(TC_M, (uint32_t)NP);
+    bool failed = false;
+
+    for (int ih = 0; ih < 2 * Ns; ++ih) {
+        int32_t off, len;
+        half_dims(d, Ns, sub_s, ih >> 1, ih & 1, &off, &len);
+        // A: row m = query b0 + m, element k; core matrix (m/8, k/8) at ((m/8)*kcols + k/8)*128 bytes
+        float qn = 0.f;
+        {
+            const int m = tid;
+            const int64_t b = b0 + m;
+            for (int k = 0; k < KP; ++k) {
+                float x = 0.f;
+                if (b < nq && k < len) x = Q[b * d + off + k];
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                const float xr = __bfloat162float(h);
+                qn = __fmaf_rn(xr, xr, qn);
+                As[(((m >> 3) * kcols + (k >> 3)) * 128 + (m & 7) * 16 + (k & 7) * 2) / 2] = __bfloat16_as_ushort(h);
+            }
+        }
+        // B: centroid c of this half, same layout with c in place of m
+        for (int c = tid; c < NP; c += TC_M) {
+            float s = 0.f;
+            for (int k = 0; k < KP; ++k) {
+                float x = 0.f;
+                if (c < sqrtK && k < len) x = cent[((int64_t)ih * sqrtK + c) * hmax + k];
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                const float xr = __bfloat162float(h);
+                s = __fmaf_rn(xr, xr, s);
+                Bs[(((c >> 3) * kcols + (k >> 3)) * 128 + (c & 7) * 16 + (k & 7) * 2) / 2] = __bfloat16_as_ushort(h);
+            }
+            cn[c] = s;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0 && !failed) {
+            for (int kk = 0; kk < KP / 16; ++kk) {
+                const uint64_t ad = smem_desc(sa(As) + (uint32_t)kk * 2u * k_step, lbo, sbo);
+                const uint64_t bd = smem_desc(sa(Bs) + (uint32_t)kk * 2u * k_step, lbo, sbo);
+                const uint32_t acc = kk > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+                         : "memory");
+        }
+        if (!failed && !mbar_wait_bounded(sa(bar), (uint32_t)(ih & 1))) {
+            failed = true;
+            if (status) atomicOr(status, 1u);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w reads lanes 32w..32w+31 (query rows), 16 columns at a time
+        const int m = tid;
+        const int64_t b = b0 + m;
+        for (int c0 = 0; c0 < NP; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(addr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (b < nq && !failed)
+                for (int j = 0; j < 16; ++j) {
+                    const int c = c0 + j;
+                    if (c < sqrtK) {
+                        const float dot = __uint_as_float(r[j]);
+                        D[(b * 2 * Ns + ih) * sqrtK + c] = __fadd_rn(__fmaf_rn(-2.f, dot, qn), cn[c]);
+                    }
+                }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // the operands and the accumulator are reused by the next half
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (failed) mbar_wait_bounded(sa(bar), (uint32_t)((2 * Ns - 1) & 1));
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+}  // namespace
+
+int rank_bf16_tables(const DeviceIndex* ix, const float* Q, int64_t nq, float* D, cudaStream_t st)
+{
+    if (nq == 0) return SUCO_OK;
+    const int KP = (ix->hmax + 15) & ~15;
+    const int NP = (ix->sqrtK + 15) & ~15;
+    int ncols = 32;
+    while (ncols < NP) ncols *= 2;
+    const size_t smem = (size_t)(TC_M + NP) * KP * 2 + (size_t)NP * 4 + 16;
+    // at least 100 KB of shared memory per CTA keeps at most two CTAs (and
+    // 2 x ncols <= 512 TMEM columns) on an SM
+    const size_t smem_req = std::max<size_t>(smem, 100 * 1024);
+    auto kern = centroid_dist_tc_kernel;
+    SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req));
+    const int64_t grid = (nq + TC_M - 1) / TC_M;
+    kern<<<(unsigned)grid, TC_M, smem_req, st>>>(Q, nq, ix->d, ix->Ns, ix->sub_s, ix->sqrtK, ix->hmax, ix->cent, KP,
+                                                 NP, ncols, D, ix->work + STATUS_WORD);
+    SUCO_CUDA_TRY(cudaGetLastError());
+    return SUCO_OK;
+}
+
+}  // namespace suco

@@ -31,7 +31,7 @@ class _QueryParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("cluster_size", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
                 ("threads", C.c_int32), ("flags", C.c_int32), ("k_per_query", C.c_void_p),
                 ("alpha_per_query", C.c_void_p), ("beta_per_query", C.c_void_p), ("precision", C.c_int32),
-                ("exact_rerank", C.c_int32), ("id_passes", C.c_int32), ("reserved0", C.c_int32)]
+                ("exact_rerank", C.c_int32), ("id_passes", C.c_int32), ("rank_precision", C.c_int32)]
 
 
 class _DebugOut(C.Structure):
@@ -84,13 +84,14 @@ def load_library():
     L.suco_adamw_step.argtypes = [vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
                                   i32, vp, vp]
     L.suco_add_reduced_copies.argtypes = [vp, i32, vp]
+    L.suco_read_status.argtypes = [vp, C.POINTER(C.c_uint32)]
     L.suco_free.argtypes = [vp]
     L.suco_free.restype = None
     L.suco_last_error.restype = C.c_char_p
     for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_query_batch", "suco_query_debug",
                  "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version",
                  "suco_kmeans_noalloc", "suco_autotune", "suco_query_features", "suco_mlp_predict",
-                 "suco_mlp_forward", "suco_mlp_backward", "suco_adamw_step", "suco_add_reduced_copies"):
+                 "suco_mlp_forward", "suco_mlp_backward", "suco_adamw_step", "suco_add_reduced_copies", "suco_read_status"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -176,29 +177,32 @@ QUERY_ONE_CLUSTER_PER_QUERY = 1
 
 
 PRECISION = {"fp32": 0, "bf16": 1}
-COPY_BF16 = 1
+COPY_BF16, COPY_RANK_BF16 = 1, 2
 
 
 def _qparams(k, alpha, beta, cluster_size, threads, nq=0, k_per_query=None, alpha_per_query=None,
-             beta_per_query=None, flags=0, precision="fp32", exact_rerank=0, id_passes=0):
+             beta_per_query=None, flags=0, precision="fp32", exact_rerank=0, id_passes=0, rank_precision="fp32"):
     return _QueryParams(int(k), int(cluster_size), float(alpha), float(beta), int(threads), int(flags),
                         _per_query(k_per_query, torch.int32, nq, "k_per_query"),
                         _per_query(alpha_per_query, torch.float32, nq, "alpha_per_query"),
                         _per_query(beta_per_query, torch.float32, nq, "beta_per_query"),
                         PRECISION[precision] if isinstance(precision, str) else int(precision), int(exact_rerank),
-                        int(id_passes), 0)
+                        int(id_passes), PRECISION[rank_precision] if isinstance(rank_precision, str)
+                        else int(rank_precision))
 
 
-def suco_add_reduced_copies(index: "SucoIndex", bf16: bool = True, stream=None):
-    """Add the reduced-precision copies of the index's dataset (BF16) used by precision="bf16"."""
-    _check(load_library().suco_add_reduced_copies(index.handle, COPY_BF16 if bf16 else 0, _stream(stream)))
+def suco_add_reduced_copies(index: "SucoIndex", bf16: bool = True, rank_bf16: bool = True, stream=None):
+    """Add the BF16 copy of the index's dataset (precision="bf16") and the
+    workspace of the BF16 tensor-core ranking (rank_precision="bf16")."""
+    mask = (COPY_BF16 if bf16 else 0) | (COPY_RANK_BF16 if rank_bf16 else 0)
+    _check(load_library().suco_add_reduced_copies(index.handle, mask, _stream(stream)))
 
 
 def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
                      out_ids: Optional[torch.Tensor] = None, out_dist: Optional[torch.Tensor] = None,
                      cluster_size: int = 0, threads: int = 0, stream=None, k_per_query=None, alpha_per_query=None,
                      beta_per_query=None, flags: int = 0, precision="fp32", exact_rerank: int = 0,
-                     id_passes: int = 0):
+                     id_passes: int = 0, rank_precision="fp32"):
     """Algorithm 4 for every row of ``queries``; returns (ids int32 [nq,k], squared dists float32 [nq,k]).
     Optional per-query CUDA tensors: k_per_query (int32), alpha_per_query, beta_per_query (float32).
     precision "bf16" re-ranks a coarse BF16 pass's exact_rerank survivors (0 = 512) exactly."""
@@ -209,7 +213,7 @@ def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
     p = _qparams(k, alpha, beta, cluster_size, threads, nq, k_per_query, alpha_per_query, beta_per_query, flags,
-                 precision, exact_rerank, id_passes)
+                 precision, exact_rerank, id_passes, rank_precision)
     _check(load_library().suco_query_batch(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out_ids),
                                            _ptr(out_dist), _stream(stream)))
     return out_ids, out_dist
@@ -218,7 +222,7 @@ def suco_query_batch(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
 def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
                      cluster_size: int = 0, threads: int = 0, want=("t_eff", "activated", "dtab", "scores", "cands"),
                      stream=None, k_per_query=None, alpha_per_query=None, beta_per_query=None, flags: int = 0,
-                     precision="fp32", exact_rerank: int = 0, id_passes: int = 0):
+                     precision="fp32", exact_rerank: int = 0, id_passes: int = 0, rank_precision="fp32"):
     """suco_query_batch plus per-stage outputs; returns a dict of CUDA tensors."""
     _dev_f32(queries, "queries")
     nq = queries.shape[0]
@@ -236,7 +240,7 @@ def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
     dbg = _DebugOut(*[(out[n].data_ptr() if n in out else None) for n in ("t_eff", "activated", "dtab", "scores",
                                                                         "cands", "survivors")])
     p = _qparams(k, alpha, beta, cluster_size, threads, nq, k_per_query, alpha_per_query, beta_per_query, flags,
-                 precision, exact_rerank, id_passes)
+                 precision, exact_rerank, id_passes, rank_precision)
     _check(load_library().suco_query_debug(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out["ids"]),
                                            _ptr(out["dist"]), C.byref(dbg), _stream(stream)))
     out["T"], out["C"] = T, Cc
@@ -343,6 +347,13 @@ def suco_free(index: SucoIndex):
     if index is not None and index.handle:
         load_library().suco_free(index.handle)
         index.handle = None
+
+
+def suco_read_status(index: SucoIndex) -> int:
+    """Read and clear the index's device status word (0: every launch completed normally)."""
+    st = C.c_uint32(0)
+    _check(load_library().suco_read_status(index.handle, C.byref(st)))
+    return int(st.value)
 
 
 def suco_last_error() -> str:

@@ -1,0 +1,106 @@
+"""BF16 tensor-core ranking (tcgen05) vs the oracle, through the C ABI.
+
+The kernel rounds the query and the centroids to BF16 and forms
+|q|^2 - 2<q,c> + |c|^2 from tensor-core inner products with FP32 accumulation.
+Its tables must match the FP64 squared distances of the same rounded vectors
+within the FP32 error of that expression; every later stage (cell activation,
+SC-scores, candidates, top-k) must then be exactly what the oracle computes
+from the GPU's own tables.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2411_14754_gb300 as pkg
+from oracle import precision_oracle as P
+from paper_2411_14754_gb300 import workloads as W
+from parity_util import assert_topk_matches
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2411_14754_gb300 import build
+    build.build()
+    pkg.load_library()
+
+
+def gpu_index(X, idx):
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(np.ascontiguousarray(X)).cuda(), idx["Ns"],
+                                               idx["sqrtK"], idx["centroids"], idx["assign"])
+    pkg.suco_add_reduced_copies(ix)
+    return ix
+
+
+def check(X, idx, Q, k, alpha, beta, sample=None, **kw):
+    ix = gpu_index(X, idx)
+    try:
+        Qd = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+        out = pkg.suco_query_debug(ix, Qd, k, alpha, beta, rank_precision="bf16", **kw)
+        full = pkg.suco_query_batch(ix, Qd, k, alpha, beta, rank_precision="bf16", **kw)
+        torch.cuda.synchronize()
+        assert pkg.suco_read_status(ix) == 0
+        host = {kk: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for kk, v in out.items()}
+    finally:
+        pkg.suco_free(ix)
+    np.testing.assert_array_equal(full[0].cpu().numpy(), host["ids"])
+    T, C = host["T"], host["C"]
+    d = X.shape[1]
+    for b in (range(len(Q)) if sample is None else sample):
+        ref, norms = P.bf16_centroid_tables(idx, Q[b])
+        L = np.array([[oracle.half_dims(d, idx["Ns"], i, h)[1] for h in range(2)] for i in range(idx["Ns"])])
+        tol = (4.0 * L[:, :, None] + 64.0) * U * norms
+        got = host["dtab"][b].astype(np.float64)
+        assert (np.abs(got - ref) <= tol).all(), np.abs(got - ref).max()
+        o = oracle.query_from_tables(X, idx, Q[b], k, T, C, got)
+        np.testing.assert_array_equal(host["t_eff"][b], o["teff"])
+        np.testing.assert_array_equal(host["activated"][b], o["activated"])
+        np.testing.assert_array_equal(host["scores"][b].astype(np.int32), o["scores"])
+        assert sorted(host["cands"][b].tolist()) == sorted(o["cands"].tolist())
+        assert_topk_matches(X, Q[b], host["ids"][b], host["dist"][b], o["ids"], o["dist"])
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = W.WORKLOADS[1]
+    X = W.dataset(1)
+    idx = oracle.build_index(X, w.Ns, w.sqrtK, w.kmeans_iters, W.kmeans_init_ids(1, w.n, w.Ns, w.sqrtK))
+    return w, X, idx
+
+
+def test_tiny_workload_tables_and_stages(tiny):
+    w, X, idx = tiny
+    check(X, idx, W.queries(1), w.k, w.alpha, w.beta)
+
+
+def test_two_launch_chunks_and_a_ragged_tail(tiny):
+    # 4096 queries per tensor-core launch: rows from both chunks and the tail tile
+    w, X, idx = tiny
+    Q = W.queries(1, nq=4096 + 301)
+    check(X, idx, Q, w.k, w.alpha, w.beta, sample=[0, 127, 128, 4095, 4096, 4200, 4396])
+
+
+@pytest.mark.parametrize("n,d,Ns,sk", [(3000, 13, 3, 16), (4000, 64, 16, 33), (20000, 24, 2, 256), (600, 8, 4, 1)])
+def test_shapes(n, d, Ns, sk):
+    # ragged halves, many subspaces, the widest codebook (N = 256), one centroid
+    X = W.random_data(21, n, d, "gauss") * np.float32(3.0)
+    Q = W.random_data(22, 40, d, "gauss") * np.float32(3.0)
+    idx = oracle.build_index(X, Ns, sk, 2, W.random_init_ids(23, n, Ns, sk))
+    check(X, idx, Q, 5, 0.05, 0.02)
+
+
+def test_needs_the_workspace(tiny):
+    w, X, idx = tiny
+    ix = pkg.suco_build_index_from_assignments(torch.from_numpy(X).cuda(), w.Ns, w.sqrtK, idx["centroids"],
+                                               idx["assign"])
+    try:
+        with pytest.raises(pkg.SucoError) as e:
+            pkg.suco_query_batch(ix, torch.from_numpy(W.queries(1)).cuda(), w.k, w.alpha, w.beta,
+                                 rank_precision="bf16")
+        assert e.value.code == -5
+    finally:
+        pkg.suco_free(ix)
