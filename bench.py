@@ -56,7 +56,11 @@ def parse():
     p.add_argument("--plain", action="store_true", help="time the fixed-ratio path at the workload's own alpha and "
                    "beta even where the workload trains the ratio network")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
-    p.add_argument("--exact-rerank", type=int, default=512, help="survivors of the BF16 coarse re-rank")
+    p.add_argument("--exact-rerank", type=int, default=512, help="survivors of the BF16/FP8 coarse re-rank")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
+                   help="re-rank precision of the fixed-ratio path")
+    p.add_argument("--rank-precision", default="fp32", choices=["fp32", "bf16"],
+                   help="centroid-distance arithmetic of the fixed-ratio path (bf16: tensor cores)")
     return p.parse_args()
 
 
@@ -633,6 +637,9 @@ def main():
     torch.cuda.synchronize()
     build_s = time.time() - t0
     del Xd
+    if args.precision != "fp32" or args.rank_precision != "fp32":
+        pkg.suco_add_reduced_copies(index)
+    qkw = dict(precision=args.precision, rank_precision=args.rank_precision, exact_rerank=args.exact_rerank)
     B = w.batch
     nb = (w.nq + B - 1) // B
     # every rank answers different batches (query-sharded replicas)
@@ -645,7 +652,7 @@ def main():
     def step(s):
         bi = order[s % nb]
         pkg.suco_query_batch(index, batches[bi], w.k, w.alpha, w.beta, out_ids=outs[bi][0], out_dist=outs[bi][1],
-                             cluster_size=args.cluster_size, threads=args.threads, stream=stream)
+                             cluster_size=args.cluster_size, threads=args.threads, stream=stream, **qkw)
         return batches[bi].shape[0]
 
     for s in range(args.warmup):
@@ -690,7 +697,7 @@ def main():
         bi = order[s % nb]
         dq[bi].copy_(hq[bi], non_blocking=True)
         pkg.suco_query_batch(index, dq[bi], w.k, w.alpha, w.beta, out_ids=outs[bi][0], out_dist=outs[bi][1],
-                             cluster_size=args.cluster_size, threads=args.threads, stream=stream)
+                             cluster_size=args.cluster_size, threads=args.threads, stream=stream, **qkw)
         hout[bi][0].copy_(outs[bi][0], non_blocking=True)
         hout[bi][1].copy_(outs[bi][1], non_blocking=True)
         return (hq[bi].numel() * 4, hout[bi][0].numel() * 4 + hout[bi][1].numel() * 4, hq[bi].shape[0])
@@ -723,9 +730,9 @@ def main():
     ns = min(args.recall_sample, batches[0].shape[0])
     q0 = batches[0][:ns]
     ids_s, dist_s = pkg.suco_query_batch(index, q0, w.k, w.alpha, w.beta, cluster_size=args.cluster_size,
-                                         threads=args.threads)
+                                         threads=args.threads, **qkw)
     dbg = pkg.suco_query_debug(index, q0, w.k, w.alpha, w.beta, cluster_size=args.cluster_size,
-                               threads=args.threads, want=("t_eff",))
+                               threads=args.threads, want=("t_eff",), **qkw)
     torch.backends.cuda.matmul.allow_tf32 = False
     Xg = torch.from_numpy(X).to(dev)
     gt = []
@@ -747,6 +754,9 @@ def main():
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     bpq = algorithmic_bytes_per_query(w, T, Cc, teff_total)
+    if args.precision != "fp32" and Cc > args.exact_rerank:
+        eb = 2.0 if args.precision == "bf16" else 1.0
+        bpq = 4.0 * teff_total + (eb * Cc + 4.0 * args.exact_rerank) * w.d
     mean_launch_ms = statistics.mean(step_ms)
     achieved = bpq * B / (mean_launch_ms / 1000.0) / 1e9
     traffic = committed_traffic(w.number)
@@ -762,15 +772,19 @@ def main():
         cpu = run_cpu_baseline(w, X, Qall, threads, target_s=args.cpu_seconds)
 
     if rank == 0:
+        cfg = workload_config(w, B)
+        if args.precision != "fp32" or args.rank_precision != "fp32":
+            cfg["workload"] += (f", re-rank {args.precision} (exact FP32 on the top {args.exact_rerank}), "
+                                f"cell ranking {args.rank_precision}")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(w, B), "recall_at_k": rec, "k": w.k,
+                "config": cfg, "recall_at_k": rec, "k": w.k,
                 "T": T, "C": Cc, "t_eff_per_query": teff_total,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                         "d2h_bytes_per_step": d2h // args.steps},
-                "clocks": clk.summary(), "gpu_launches": args.steps,
+                "clocks": clk.summary(), "gpu_launches": args.steps * (2 if args.rank_precision == "bf16" else 1),
                 "index_build_s": build_s}
         print(json.dumps(line), flush=True)
     pkg.suco_free(index)

@@ -122,6 +122,11 @@ SUCO_API int suco_build_index_from_assignments(const float* data, int64_t n, int
  * equals FP32's. */
 #define SUCO_PRECISION_FP32 0
 #define SUCO_PRECISION_BF16 1
+/* FP8 (not in the paper): the same coarse pass from the index's FP8 E4M3 copy,
+ * each value stored as e4m3(x / s_i) with one FP32 scale s_i = max|x| / 448
+ * per subspace i (quotient in FP32, round to nearest even, saturating), and
+ * decoded as code * s_i in FP32. */
+#define SUCO_PRECISION_FP8 2
 
 /* suco_query_params.rank_precision: how the half-subspace centroid distances
  * that rank the IMI cells (Algorithm 4, then Algorithm 3) are computed.
@@ -140,12 +145,12 @@ typedef struct suco_query_params {
     int32_t cluster_size; /* CTAs cooperating on one query (1,2,4,8,16); 0 = automatic  */
     double alpha;         /* collision ratio, 0 < alpha <= 1                            */
     double beta;          /* re-rank ratio,   0 < beta  <= 1 (bound of beta_per_query)   */
-    int32_t threads;      /* threads per CTA (512 or 1024); 0 = automatic               */
+    int32_t threads;      /* threads per CTA (256, 512 or 1024); 0 = automatic          */
     int32_t flags;        /* SUCO_QUERY_* bits, 0 by default                            */
     const int32_t* k_per_query;    /* (device, nullable) [nq], clamped to [1, k]        */
     const float* alpha_per_query;  /* (device, nullable) [nq], clamped to (0, 1]        */
     const float* beta_per_query;   /* (device, nullable) [nq], clamped to (0, beta]     */
-    int32_t precision;    /* SUCO_PRECISION_*; BF16 needs suco_add_reduced_copies      */
+    int32_t precision;    /* SUCO_PRECISION_*; BF16/FP8 need suco_add_reduced_copies   */
     int32_t exact_rerank; /* R: survivors of the coarse pass (0 = 512), up to 2^24       */
     int32_t id_passes;    /* passes over the id range (0 = automatic: the fewest whose
                              SC-score counters fit on chip; else a power of two); the
@@ -175,7 +180,7 @@ typedef struct suco_query_debug_out {
     int32_t* cands;      /* (device) [nq][C] candidate ids in ascending id order: every id
                             scoring above the cut and the lowest-id ties at the cut       */
     uint8_t* survivors;  /* (device) [nq][n], zeroed by the caller: set to 1 for every
-                            candidate that survives the BF16 coarse pass                    */
+                            candidate that survives the BF16/FP8 coarse pass                */
 } suco_query_debug_out;
 
 /* suco_query_batch plus the per-stage outputs above (same arguments). */
@@ -192,6 +197,9 @@ SUCO_API int suco_query_debug(const suco_index* index, const float* queries, int
 /* mask bit 1 (SUCO_COPY_RANK_BF16): reserve the workspace of the BF16
  * tensor-core ranking, 4096 x Ns x 2 x sqrtK FP32 values. */
 #define SUCO_COPY_RANK_BF16 2
+/* mask bit 2 (SUCO_COPY_FP8): the FP8 E4M3 copy (n x ceil16(d) bytes, zero
+ * padded) and its per-subspace scales; it serves SUCO_PRECISION_FP8. */
+#define SUCO_COPY_FP8 4
 SUCO_API int suco_add_reduced_copies(suco_index* index, int32_t mask, void* stream);
 
 /* Times every launch shape (cluster size x threads per CTA) that fits, on the

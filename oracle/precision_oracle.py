@@ -84,14 +84,16 @@ def e4m3_to_f64(c):
 
 def subspace_scales_e4m3(X, Ns):
     """One scale per subspace: the largest |x| over the subspace's columns
-    divided by 448 (1 where the subspace is all zero)."""
-    X = np.asarray(X, dtype=np.float64)
+    divided by 448 (1 where the subspace is all zero).  The scale is an FP32
+    number (the quotient rounded to FP32), because the code of every value is
+    decided from the FP32 quotient x / scale."""
+    X = np.asarray(X, dtype=np.float32)
     d = X.shape[1]
-    s = np.empty(Ns, dtype=np.float64)
+    s = np.empty(Ns, dtype=np.float32)
     for i in range(Ns):
         off, ln = _o.subspace_dims(d, Ns, i)
-        m = np.abs(X[:, off:off + ln]).max() if X.shape[0] else 0.0
-        s[i] = m / 448.0 if m > 0 else 1.0
+        m = np.float32(np.abs(X[:, off:off + ln]).max()) if X.shape[0] else np.float32(0.0)
+        s[i] = np.float32(m / np.float32(448.0)) if m > 0 else np.float32(1.0)
     return s
 
 
@@ -110,8 +112,9 @@ def decoded_rows(X, precision, Ns=None, scales=None):
     if precision == 1:
         return bf16_to_f64(round_bf16(X))
     if precision == 2:
-        col = column_scales(scales, X.shape[1], Ns)
-        return e4m3_to_f64(quantize_e4m3(X.astype(np.float64) / col[None, :])) * col[None, :]
+        col32 = column_scales(scales, X.shape[1], Ns).astype(np.float32)
+        quot = (X / col32[None, :]).astype(np.float32)  # IEEE FP32 quotient, round to nearest
+        return e4m3_to_f64(quantize_e4m3(quot.astype(np.float64))) * col32.astype(np.float64)[None, :]
     raise ValueError(precision)
 
 

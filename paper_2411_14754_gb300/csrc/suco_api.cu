@@ -71,6 +71,10 @@ void free_index_memory(DeviceIndex* ix)
     cudaFree(ix->work);
     cudaFree(ix->Xh);
     cudaFree(ix->rank_ws);
+    cudaFree(ix->X8);
+    cudaFree(ix->s8col);
+    ix->X8 = nullptr;
+    ix->s8col = nullptr;
     ix->Xh = nullptr;
     ix->rank_ws = nullptr;
     ix->work = nullptr;
@@ -149,10 +153,13 @@ int check_query_params(const suco_index* index, const float* queries, int64_t nq
     if (!(p->alpha > 0.0 && p->alpha <= 1.0)) return fail(SUCO_EINVAL, "alpha=%g must be in (0, 1]", p->alpha);
     if (!(p->beta > 0.0 && p->beta <= 1.0)) return fail(SUCO_EINVAL, "beta=%g must be in (0, 1]", p->beta);
     if (p->flags & ~SUCO_QUERY_ONE_CLUSTER_PER_QUERY) return fail(SUCO_EINVAL, "unknown flags 0x%x", p->flags);
-    if (p->precision != SUCO_PRECISION_FP32 && p->precision != SUCO_PRECISION_BF16)
-        return fail(SUCO_EINVAL, "precision=%d must be SUCO_PRECISION_FP32 or SUCO_PRECISION_BF16", p->precision);
+    if (p->precision != SUCO_PRECISION_FP32 && p->precision != SUCO_PRECISION_BF16 &&
+        p->precision != SUCO_PRECISION_FP8)
+        return fail(SUCO_EINVAL, "precision=%d must be SUCO_PRECISION_FP32, _BF16 or _FP8", p->precision);
     if (p->precision == SUCO_PRECISION_BF16 && !index->ix.Xh)
         return fail(SUCO_ESTATE, "the index has no BF16 copy: call suco_add_reduced_copies first");
+    if (p->precision == SUCO_PRECISION_FP8 && !index->ix.X8)
+        return fail(SUCO_ESTATE, "the index has no FP8 copy: call suco_add_reduced_copies first");
     if (p->id_passes < 0) return fail(SUCO_EINVAL, "id_passes=%d must not be negative", p->id_passes);
     if (p->rank_precision != SUCO_RANK_FP32 && p->rank_precision != SUCO_RANK_BF16)
         return fail(SUCO_EINVAL, "rank_precision=%d must be SUCO_RANK_FP32 or SUCO_RANK_BF16", p->rank_precision);
@@ -304,7 +311,7 @@ int suco_autotune(suco_index* index, const float* queries, int64_t nq, const suc
     SUCO_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     int best_cl = 0, best_nt = 0;
-    const int cls[] = {1, 2, 4, 8, 16}, nts[] = {512, 1024};
+    const int cls[] = {1, 2, 4, 8, 16}, nts[] = {256, 512, 1024};
     for (int cl : cls)
         for (int nt : nts) {
             suco_query_params q = *params;

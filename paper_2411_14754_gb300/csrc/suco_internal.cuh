@@ -40,6 +40,9 @@ struct DeviceIndex {
     float* X = nullptr;           // [n][ld]; columns d..ld-1 are zero
     uint16_t* Xh = nullptr;       // optional BF16 copy of X, [n][ldh] (ldh = d rounded up to 8), padding zero
     float* rank_ws = nullptr;     // optional [RANK_CHUNK][Ns][2][sqrtK] centroid-distance tables (BF16 ranking)
+    uint8_t* X8 = nullptr;        // optional FP8 E4M3 copy of X / scale, [n][ld8] (ld8 = d rounded up to 16)
+    float* s8col = nullptr;       // [ld8] scale of every column (its subspace's), 0 past d
+    int64_t ld8 = 0;
     int64_t ldh = 0;
     float* cent = nullptr;        // [Ns][2][sqrtK][hmax]; padding zero
     uint32_t* cell_off = nullptr; // [Ns][K+1] offsets into perm[i]

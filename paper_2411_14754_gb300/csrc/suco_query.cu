@@ -43,6 +43,9 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "suco_internal.cuh"
 
 namespace suco {
@@ -92,6 +95,9 @@ struct QArgs {
     uint32_t o_run, run_stride;        // running candidate list of a multi-pass query: ids [2][stride], scores [2][stride]
     int32_t nch;                       // id chunks of the index (rows of split per subspace, minus one)
     const float* dtab_in;              // [nq][Ns][2][sqrtK] centroid distances computed before (BF16 ranking) or null
+    const uint8_t* __restrict__ X8;    // FP8 E4M3 copy of X / column scale, [n][ld8] (precision 2)
+    int64_t ld8;
+    const float* __restrict__ s8col;   // [ld8] column scales of the FP8 copy
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -931,6 +937,90 @@ __device__ void rerank_bf16(const QArgs& A, const float4* q4, const uint32_t* id
     }
 }
 
+// four E4M3 codes (byte j of w is element j) decoded exactly, times their scales
+__device__ __forceinline__ float4 e4m3x4_scaled(uint32_t w, float4 s)
+{
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+    return make_float4(__fmul_rn(a.x, s.x), __fmul_rn(a.y, s.y), __fmul_rn(b.x, s.z), __fmul_rn(b.y, s.w));
+}
+
+__device__ __forceinline__ float sqdiff4(float4 x, float4 q, float acc)
+{
+    float df = __fsub_rn(x.x, q.x);
+    acc = __fmaf_rn(df, df, acc);
+    df = __fsub_rn(x.y, q.y);
+    acc = __fmaf_rn(df, df, acc);
+    df = __fsub_rn(x.z, q.z);
+    acc = __fmaf_rn(df, df, acc);
+    df = __fsub_rn(x.w, q.w);
+    return __fmaf_rn(df, df, acc);
+}
+
+// S6 coarse pass on the FP8 copy: 16 codes per 16-byte chunk, decoded as
+// code * column scale in FP32, squared differences summed in FP32 in element
+// order per lane, then over the 8 lanes of the row.
+template <int NT>
+__device__ void rerank_fp8(const QArgs& A, const float4* q4, const uint32_t* ids, uint32_t count,
+                           unsigned long long* keys)
+{
+    constexpr int NW = NT / 32;
+    constexpr int CH = 2;  // chunks per lane per row in one load round
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane >> 3, gl = lane & 7;
+    const int ldc = (int)(A.ld8 / 16);
+    const uint4* X16 = reinterpret_cast<const uint4*>(A.X8);
+    const float4* s4 = reinterpret_cast<const float4*>(A.s8col);
+    for (uint32_t rb = (uint32_t)warp * 8u; rb < count; rb += (uint32_t)NW * 8u) {
+        const uint32_t ra = rb + (uint32_t)grp, rc = ra + 4u;
+        const uint32_t ida = ra < count ? ids[ra] : 0xffffffffu;
+        const uint32_t idc = rc < count ? ids[rc] : 0xffffffffu;
+        const bool va = ida < (uint32_t)A.n, vc = idc < (uint32_t)A.n;
+        const uint4* pa = X16 + (int64_t)(va ? ida : 0u) * ldc;
+        const uint4* pc = X16 + (int64_t)(vc ? idc : 0u) * ldc;
+        float acc_a = 0.f, acc_c = 0.f;
+        for (int c0 = gl; c0 < ldc; c0 += 8 * CH) {
+            uint4 xa[CH], xc[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int c = c0 + 8 * u;
+                xa[u] = make_uint4(0u, 0u, 0u, 0u);
+                xc[u] = xa[u];
+                if (c < ldc) {
+                    if (va) xa[u] = ldg_stream_u4(pa + c);
+                    if (vc) xc[u] = ldg_stream_u4(pc + c);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int c = c0 + 8 * u;
+                if (c < ldc) {
+                    const uint32_t wa[4] = {xa[u].x, xa[u].y, xa[u].z, xa[u].w};
+                    const uint32_t wc[4] = {xc[u].x, xc[u].y, xc[u].z, xc[u].w};
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float4 sc = __ldg(s4 + 4 * c + v);
+                        const float4 qv = q4[4 * c + v];
+                        acc_a = sqdiff4(e4m3x4_scaled(wa[v], sc), qv, acc_a);
+                        acc_c = sqdiff4(e4m3x4_scaled(wc[v], sc), qv, acc_c);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            acc_a = __fadd_rn(acc_a, __shfl_xor_sync(0xffffffffu, acc_a, o));
+            acc_c = __fadd_rn(acc_c, __shfl_xor_sync(0xffffffffu, acc_c, o));
+        }
+        if (gl == 0) {
+            if (ra < count) keys[ra] = va ? ((unsigned long long)__float_as_uint(acc_a) << 32) | ida : ~0ull;
+            if (rc < count) keys[rc] = vc ? ((unsigned long long)__float_as_uint(acc_c) << 32) | idc : ~0ull;
+        }
+    }
+}
+
 // The key of rank R (1-based) among the keys of every CTA of the cluster
 // (keys are unique), by a radix select over 8-bit digits from the top: each
 // pass every CTA histograms its keys that match the decided prefix, publishes
@@ -1008,7 +1098,7 @@ __device__ unsigned long long cluster_rank_cut(const QArgs& A, char* smem, const
 }
 
 template <int NT, int NSMAX>
-__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const QArgs A)
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_query_kernel(const QArgs A)
 {
     extern __shared__ __align__(16) char smem[];
     constexpr int B = NSMAX == 8 ? 4 : (NSMAX == 16 ? 5 : 6);
@@ -1220,52 +1310,74 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
         }
         for (int t = threadIdx.x; t < CL; t += NT) slot_base[t] = map_rank(smem_addr(ids_out), (uint32_t)t);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            // the cut over the list entries and this pass's ids together
-            uint32_t total = 0;
-            for (int rr = 0; rr < CL; ++rr) total += allc[rr * 2 * NC] + allc[rr * 2 * NC + NC];
-            const uint32_t keep = min(qC, total);
-            int theta = 0;
-            for (int s = A.Ns; s >= 1; --s) {
-                uint32_t tot = 0;
-                for (int rr = 0; rr < CL; ++rr) tot += allc[rr * 2 * NC + s] + allc[rr * 2 * NC + NC + s];
-                if (tot >= keep) {
-                    theta = s;
-                    break;
-                }
-            }
-            // output order: the list entries (CTA order), then this pass's ids (CTA order = id order)
-            uint32_t RG = 0, RE = 0, rg_pre = 0, re_pre = 0, PG = 0, pg_pre = 0, pe_pre = 0;
+        if (warp == 0) {
+            // the cut over the list entries and this pass's ids together, by
+            // one warp: lane l sums the counts of score >= l+1 over the CTAs
+            uint32_t total = 0, tot_s = 0;
+            const int s1 = lane + 1;
             for (int rr = 0; rr < CL; ++rr) {
                 const uint32_t* cp = allc + rr * 2 * NC;
+                total += cp[0] + cp[NC];
+                if (s1 <= A.Ns) tot_s += cp[s1] + cp[NC + s1];
+            }
+            const uint32_t keep = min(qC, total);
+            // counts fall as s grows, so the lanes that reach keep are a prefix
+            const int theta = __popc(__ballot_sync(0xffffffffu, s1 <= A.Ns && tot_s >= keep));
+            // per-CTA splits at theta: lane rr < CL
+            uint32_t rgt = 0, req = 0, pgt = 0, peq = 0;
+            if (lane < CL) {
+                const uint32_t* cp = allc + lane * 2 * NC;
                 const uint32_t* cr = cp + NC;
-                const uint32_t rgt = cr[theta + 1], req = cr[theta] - rgt;
-                const uint32_t pgt = cp[theta + 1], peq = cp[theta] - pgt;
-                if (rr < (int)r) {
-                    rg_pre += rgt;
-                    re_pre += req;
-                    pg_pre += pgt;
-                    pe_pre += peq;
+                rgt = cr[theta + 1];
+                req = cr[theta] - rgt;
+                pgt = cp[theta + 1];
+                peq = cp[theta] - pgt;
+            }
+            uint32_t x_rg = rgt, x_re = req, x_pg = pgt, x_pe = peq;  // inclusive scans over the CTAs
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t a1 = __shfl_up_sync(0xffffffffu, x_rg, o), a2 = __shfl_up_sync(0xffffffffu, x_re, o);
+                const uint32_t a3 = __shfl_up_sync(0xffffffffu, x_pg, o), a4 = __shfl_up_sync(0xffffffffu, x_pe, o);
+                if (lane >= o) {
+                    x_rg += a1;
+                    x_re += a2;
+                    x_pg += a3;
+                    x_pe += a4;
                 }
-                RG += rgt;
-                RE += req;
-                PG += pgt;
             }
+            const uint32_t RG = __shfl_sync(0xffffffffu, x_rg, 31), RE = __shfl_sync(0xffffffffu, x_re, 31);
+            const uint32_t PG = __shfl_sync(0xffffffffu, x_pg, 31);
+            // this CTA's exclusive prefixes (lane r holds the inclusive ones)
+            const uint32_t rg_pre = __shfl_sync(0xffffffffu, x_rg - rgt, (int)r);
+            const uint32_t re_pre = __shfl_sync(0xffffffffu, x_re - req, (int)r);
+            const uint32_t pg_pre = __shfl_sync(0xffffffffu, x_pg - pgt, (int)r);
+            const uint32_t pe_pre = __shfl_sync(0xffffffffu, x_pe - peq, (int)r);
             // per-warp bases of this pass's ids: entries of the output order before the warp's range
-            uint32_t sg = RG + pg_pre, se = RE + pe_pre;
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t gt = wcnt[w * NC + theta + 1];
-                const uint32_t eq = wcnt[w * NC + theta] - gt;
-                wbase[2 * w] = sg;
-                wbase[2 * w + 1] = se;
-                sg += gt;
-                se += eq;
+            uint32_t gt = 0, eq = 0;
+            if (lane < NW) {
+                gt = wcnt[lane * NC + theta + 1];
+                eq = wcnt[lane * NC + theta] - gt;
             }
-            sel[0] = (uint32_t)theta;
-            sel[1] = keep;
-            sel[2] = keep - (RG + PG);  // entries scoring exactly theta that are kept (the lowest ids)
-            sel[3] = rg_pre;
-            sel[4] = re_pre;
+            uint32_t x_g = gt, x_e = eq;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t a1 = __shfl_up_sync(0xffffffffu, x_g, o), a2 = __shfl_up_sync(0xffffffffu, x_e, o);
+                if (lane >= o) {
+                    x_g += a1;
+                    x_e += a2;
+                }
+            }
+            if (lane < NW) {
+                wbase[2 * lane] = RG + pg_pre + x_g - gt;
+                wbase[2 * lane + 1] = RE + pe_pre + x_e - eq;
+            }
+            if (lane == 0) {
+                sel[0] = (uint32_t)theta;
+                sel[1] = keep;
+                sel[2] = keep - (RG + PG);  // entries scoring exactly theta that are kept (the lowest ids)
+                sel[3] = rg_pre;
+                sel[4] = re_pre;
+            }
         }
         __syncthreads();
         const uint32_t theta = sel[0], keep = sel[1], need_eq = sel[2];
@@ -1375,7 +1487,10 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) suco_query_kernel(const
     } else {
         // coarse pass on the reduced-precision copy, then the R smallest
         // coarse keys of the whole cluster survive into the exact pass
-        rerank_bf16<NT>(A, q4, slots, mine, keys);
+        if (A.precision == 1)
+            rerank_bf16<NT>(A, q4, slots, mine, keys);
+        else
+            rerank_fp8<NT>(A, q4, slots, mine, keys);
         __syncthreads();
         const unsigned long long cut = cluster_rank_cut<NT>(A, smem, keys, mine, A.R);
         uint32_t* ns = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 106;
@@ -1728,6 +1843,23 @@ int launch_t(const Layout& L, int64_t nq, bool persistent, uint32_t* work, cudaS
     return SUCO_OK;
 }
 
+int dispatch(const Layout& L, int NT, int nsmax, int64_t nq, bool persistent, uint32_t* work, cudaStream_t st)
+{
+    if (NT == 1024) {
+        if (nsmax == 8) return launch_t<1024, 8>(L, nq, persistent, work, st);
+        if (nsmax == 16) return launch_t<1024, 16>(L, nq, persistent, work, st);
+        return launch_t<1024, 32>(L, nq, persistent, work, st);
+    }
+    if (NT == 256) {
+        if (nsmax == 8) return launch_t<256, 8>(L, nq, persistent, work, st);
+        if (nsmax == 16) return launch_t<256, 16>(L, nq, persistent, work, st);
+        return launch_t<256, 32>(L, nq, persistent, work, st);
+    }
+    if (nsmax == 8) return launch_t<512, 8>(L, nq, persistent, work, st);
+    if (nsmax == 16) return launch_t<512, 16>(L, nq, persistent, work, st);
+    return launch_t<512, 32>(L, nq, persistent, work, st);
+}
+
 }  // namespace
 
 int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_query_params* p, int32_t* ids,
@@ -1738,7 +1870,8 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     thresholds(ix->n, p->alpha, p->beta, p->k, &T, &C);
     const int nsmax = ix->Ns <= 8 ? 8 : (ix->Ns <= 16 ? 16 : 32);
     int NT = p->threads;
-    if (NT != 0 && NT != 512 && NT != 1024) return fail(SUCO_EINVAL, "threads must be 0, 512 or 1024 (got %d)", NT);
+    if (NT != 0 && NT != 256 && NT != 512 && NT != 1024)
+        return fail(SUCO_EINVAL, "threads must be 0, 256, 512 or 1024 (got %d)", NT);
     int CL = p->cluster_size;
     if (CL == 0 && NT == 0)
         for (const auto& t : ix->tuned)
@@ -1817,6 +1950,9 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     A.R = (uint32_t)(p->exact_rerank > 0 ? p->exact_rerank : 512);
     A.Xh = ix->Xh;
     A.ldh = ix->ldh;
+    A.X8 = ix->X8;
+    A.ld8 = ix->ld8;
+    A.s8col = ix->s8col;
 
     if (dbg) {
         A.dbg_teff = dbg->t_eff;
@@ -1852,15 +1988,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
             if (base.dbg_surv) C2.dbg_surv = base.dbg_surv + c0 * base.n;
             uint32_t* work = ix->work + (size_t)WORK_STRIDE * (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next,
                                                                                 1u, __ATOMIC_RELAXED) % WORK_SLOTS);
-            if (NT == 1024) {
-                if (nsmax == 8) rc = launch_t<1024, 8>(L, cnt, persistent, work, st);
-                else if (nsmax == 16) rc = launch_t<1024, 16>(L, cnt, persistent, work, st);
-                else rc = launch_t<1024, 32>(L, cnt, persistent, work, st);
-            } else {
-                if (nsmax == 8) rc = launch_t<512, 8>(L, cnt, persistent, work, st);
-                else if (nsmax == 16) rc = launch_t<512, 16>(L, cnt, persistent, work, st);
-                else rc = launch_t<512, 32>(L, cnt, persistent, work, st);
-            }
+            rc = dispatch(L, NT, nsmax, cnt, persistent, work, st);
             if (rc) return rc;
         }
         return SUCO_OK;
@@ -1869,14 +1997,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     uint32_t* work = ix->work + (size_t)WORK_STRIDE *
                                     (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next, 1u,
                                                         __ATOMIC_RELAXED) % WORK_SLOTS);
-    if (NT == 1024) {
-        if (nsmax == 8) return launch_t<1024, 8>(L, nq, persistent, work, st);
-        if (nsmax == 16) return launch_t<1024, 16>(L, nq, persistent, work, st);
-        return launch_t<1024, 32>(L, nq, persistent, work, st);
-    }
-    if (nsmax == 8) return launch_t<512, 8>(L, nq, persistent, work, st);
-    if (nsmax == 16) return launch_t<512, 16>(L, nq, persistent, work, st);
-    return launch_t<512, 32>(L, nq, persistent, work, st);
+    return dispatch(L, NT, nsmax, nq, persistent, work, st);
 }
 
 }  // namespace suco

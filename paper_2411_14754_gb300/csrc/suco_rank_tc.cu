@@ -8,8 +8,8 @@
 // with the inner products from tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in
 // tensor memory) and the squared norms of the rounded vectors summed in FP32.
 //
-// One CTA of 128 threads handles 128 queries and every half-subspace in turn:
-// the threads stage both operands in shared memory in the canonical K-major
+// One CTA of 128 threads handles 128 queries and one half-subspace: the
+// threads stage both operands in shared memory in the canonical K-major
 // layout without swizzle (core matrices of 8 rows x 16 bytes), one thread
 // issues the MMAs into a 128-lane x NP-column FP32 accumulator, a commit
 // arrives on an mbarrier, and each warp reads its 32 lanes back with
@@ -79,7 +79,7 @@ __device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 constexpr int TC_M = 128;
 
 // dynamic shared memory: A [128 x KP] bf16, B [NP x KP] bf16, |c|^2 [NP] f32,
-// mbarrier (8 B), TMEM address (4 B)
+// mbarrier (8 B), TMEM address (4 B).  grid = (query tiles, 2*Ns halves).
 __global__ void __launch_bounds__(128, 1)
     centroid_dist_tc_kernel(const float* __restrict__ Q, int64_t nq, int32_t d, int32_t Ns, int32_t sub_s,
                             int32_t sqrtK, int32_t hmax, const float* __restrict__ cent, int32_t KP, int32_t NP,
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(128, 1)
     uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t b0 = (int64_t)blockIdx.x * TC_M;
+    const int ih = (int)blockIdx.y;
     const int kcols = KP / 8;  // core-matrix columns along K
 
     if (warp == 0) {
@@ -105,6 +106,53 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    int32_t off, len;
+    half_dims(d, Ns, sub_s, ih >> 1, ih & 1, &off, &len);
+    // A: row m = query b0 + m; the 8 values of core-matrix column kc of a row
+    // are one 16-byte store at ((m/8)*kcols + kc)*128 + (m%8)*16
+    float qn = 0.f;
+    {
+        const int m = tid;
+        const int64_t b = b0 + m;
+        for (int kc = 0; kc < kcols; ++kc) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const int k = kc * 8 + e;
+                const float x0 = (b < nq && k < len) ? Q[b * d + off + k] : 0.f;
+                const float x1 = (b < nq && k + 1 < len) ? Q[b * d + off + k + 1] : 0.f;
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                const float r0 = __bfloat162float(h0), r1 = __bfloat162float(h1);
+                qn = __fmaf_rn(r0, r0, qn);
+                qn = __fmaf_rn(r1, r1, qn);
+                w[e >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            }
+            *reinterpret_cast<uint4*>(reinterpret_cast<char*>(As) + ((m >> 3) * kcols + kc) * 128 + (m & 7) * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    // B: centroid c of this half, same layout with c in place of m
+    for (int c = tid; c < NP; c += TC_M) {
+        float s = 0.f;
+        for (int kc = 0; kc < kcols; ++kc) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const int k = kc * 8 + e;
+                const float x0 = (c < sqrtK && k < len) ? cent[((int64_t)ih * sqrtK + c) * hmax + k] : 0.f;
+                const float x1 = (c < sqrtK && k + 1 < len) ? cent[((int64_t)ih * sqrtK + c) * hmax + k + 1] : 0.f;
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                const float r0 = __bfloat162float(h0), r1 = __bfloat162float(h1);
+                s = __fmaf_rn(r0, r0, s);
+                s = __fmaf_rn(r1, r1, s);
+                w[e >> 1] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            }
+            *reinterpret_cast<uint4*>(reinterpret_cast<char*>(Bs) + ((c >> 3) * kcols + kc) * 128 + (c & 7) * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        cn[c] = s;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -112,64 +160,26 @@ __global__ void __launch_bounds__(128, 1)
     // byte offsets between core matrices: along K (the descriptor's leading
     // byte offset) and along M or N (its stride byte offset)
     const uint32_t k_step = 128u, mn_step = (uint32_t)kcols * 128u;
-    const uint32_t lbo = k_step, sbo = mn_step;
-    const uint32_t idesc = instr_desc_bf16(TC_M, (uint32_t)NP);
-    bool failed = false;
-
-    for (int ih = 0; ih < 2 * Ns; ++ih) {
-        int32_t off, len;
-        half_dims(d, Ns, sub_s, ih >> 1, ih & 1, &off, &len);
-        // A: row m = query b0 + m, element k; core matrix (m/8, k/8) at ((m/8)*kcols + k/8)*128 bytes
-        float qn = 0.f;
-        {
-            const int m = tid;
-            const int64_t b = b0 + m;
-            for (int k = 0; k < KP; ++k) {
-                float x = 0.f;
-                if (b < nq && k < len) x = Q[b * d + off + k];
-                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                const float xr = __bfloat162float(h);
-                qn = __fmaf_rn(xr, xr, qn);
-                As[(((m >> 3) * kcols + (k >> 3)) * 128 + (m & 7) * 16 + (k & 7) * 2) / 2] = __bfloat16_as_ushort(h);
-            }
+    if (tid == 0) {
+        const uint32_t idesc = instr_desc_bf16(TC_M, (uint32_t)NP);
+        for (int kk = 0; kk < KP / 16; ++kk) {
+            const uint64_t ad = smem_desc(sa(As) + (uint32_t)kk * 2u * k_step, k_step, mn_step);
+            const uint64_t bd = smem_desc(sa(Bs) + (uint32_t)kk * 2u * k_step, k_step, mn_step);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
         }
-        // B: centroid c of this half, same layout with c in place of m
-        for (int c = tid; c < NP; c += TC_M) {
-            float s = 0.f;
-            for (int k = 0; k < KP; ++k) {
-                float x = 0.f;
-                if (c < sqrtK && k < len) x = cent[((int64_t)ih * sqrtK + c) * hmax + k];
-                const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                const float xr = __bfloat162float(h);
-                s = __fmaf_rn(xr, xr, s);
-                Bs[(((c >> 3) * kcols + (k >> 3)) * 128 + (c & 7) * 16 + (k & 7) * 2) / 2] = __bfloat16_as_ushort(h);
-            }
-            cn[c] = s;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0 && !failed) {
-            for (int kk = 0; kk < KP / 16; ++kk) {
-                const uint64_t ad = smem_desc(sa(As) + (uint32_t)kk * 2u * k_step, lbo, sbo);
-                const uint64_t bd = smem_desc(sa(Bs) + (uint32_t)kk * 2u * k_step, lbo, sbo);
-                const uint32_t acc = kk > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
-                         : "memory");
-        }
-        if (!failed && !mbar_wait_bounded(sa(bar), (uint32_t)(ih & 1))) {
-            failed = true;
-            if (status) atomicOr(status, 1u);
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: warp w reads lanes 32w..32w+31 (query rows), 16 columns at a time
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+                     : "memory");
+    }
+    const bool ok = mbar_wait_bounded(sa(bar), 0u);
+    if (!ok && status) atomicOr(status, 1u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w reads lanes 32w..32w+31 (query rows), 16 columns at a time
+    {
         const int m = tid;
         const int64_t b = b0 + m;
         for (int c0 = 0; c0 < NP; c0 += 16) {
@@ -184,7 +194,7 @@ __global__ void __launch_bounds__(128, 1)
                 : "r"(addr)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (b < nq && !failed)
+            if (b < nq && ok)
                 for (int j = 0; j < 16; ++j) {
                     const int c = c0 + j;
                     if (c < sqrtK) {
@@ -193,12 +203,12 @@ __global__ void __launch_bounds__(128, 1)
                     }
                 }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // the operands and the accumulator are reused by the next half
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (failed) mbar_wait_bounded(sa(bar), (uint32_t)((2 * Ns - 1) & 1));
+    // an MMA still in flight after a wait that gave up: one more bounded wait
+    if (!ok) mbar_wait_bounded(sa(bar), 0u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
@@ -218,8 +228,8 @@ int rank_bf16_tables(const DeviceIndex* ix, const float* Q, int64_t nq, float* D
     const size_t smem_req = std::max<size_t>(smem, 100 * 1024);
     auto kern = centroid_dist_tc_kernel;
     SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req));
-    const int64_t grid = (nq + TC_M - 1) / TC_M;
-    kern<<<(unsigned)grid, TC_M, smem_req, st>>>(Q, nq, ix->d, ix->Ns, ix->sub_s, ix->sqrtK, ix->hmax, ix->cent, KP,
+    const int64_t tiles = (nq + TC_M - 1) / TC_M;
+    kern<<<dim3((unsigned)tiles, (unsigned)(2 * ix->Ns)), TC_M, smem_req, st>>>(Q, nq, ix->d, ix->Ns, ix->sub_s, ix->sqrtK, ix->hmax, ix->cent, KP,
                                                  NP, ncols, D, ix->work + STATUS_WORD);
     SUCO_CUDA_TRY(cudaGetLastError());
     return SUCO_OK;

@@ -176,8 +176,8 @@ def _per_query(t, dtype, nq, name):
 QUERY_ONE_CLUSTER_PER_QUERY = 1
 
 
-PRECISION = {"fp32": 0, "bf16": 1}
-COPY_BF16, COPY_RANK_BF16 = 1, 2
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+COPY_BF16, COPY_RANK_BF16, COPY_FP8 = 1, 2, 4
 
 
 def _qparams(k, alpha, beta, cluster_size, threads, nq=0, k_per_query=None, alpha_per_query=None,
@@ -191,10 +191,11 @@ def _qparams(k, alpha, beta, cluster_size, threads, nq=0, k_per_query=None, alph
                         else int(rank_precision))
 
 
-def suco_add_reduced_copies(index: "SucoIndex", bf16: bool = True, rank_bf16: bool = True, stream=None):
-    """Add the BF16 copy of the index's dataset (precision="bf16") and the
-    workspace of the BF16 tensor-core ranking (rank_precision="bf16")."""
-    mask = (COPY_BF16 if bf16 else 0) | (COPY_RANK_BF16 if rank_bf16 else 0)
+def suco_add_reduced_copies(index: "SucoIndex", bf16: bool = True, rank_bf16: bool = True, fp8: bool = True,
+                            stream=None):
+    """Add the BF16 and FP8 copies of the index's dataset (precision="bf16" /
+    "fp8") and the workspace of the BF16 tensor-core ranking (rank_precision="bf16")."""
+    mask = (COPY_BF16 if bf16 else 0) | (COPY_RANK_BF16 if rank_bf16 else 0) | (COPY_FP8 if fp8 else 0)
     _check(load_library().suco_add_reduced_copies(index.handle, mask, _stream(stream)))
 
 

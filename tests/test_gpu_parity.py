@@ -64,7 +64,7 @@ def test_tiny_workload_all_queries(tiny):
 
 @pytest.mark.parametrize("cluster_size", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("flags", [0, 1])
-@pytest.mark.parametrize("threads", [512, 1024])
+@pytest.mark.parametrize("threads", [256, 512, 1024])
 def test_tiny_workload_every_launch_shape(tiny, cluster_size, threads, flags):
     w, X, Q, idx = tiny
     run(X, idx, Q[:24], w.k, w.alpha, w.beta, cluster_size=cluster_size, threads=threads, flags=flags)
@@ -174,7 +174,7 @@ def test_argument_errors_on_device(tiny):
                                                idx["assign"])
     Qd = torch.from_numpy(Q[:2]).to(dev)
     for kw in (dict(k=0, alpha=0.05, beta=0.01), dict(k=10, alpha=0.0, beta=0.01), dict(k=10, alpha=0.05, beta=1.5),
-               dict(k=10, alpha=0.05, beta=0.01, cluster_size=3), dict(k=10, alpha=0.05, beta=0.01, threads=256),
+               dict(k=10, alpha=0.05, beta=0.01, cluster_size=3), dict(k=10, alpha=0.05, beta=0.01, threads=384),
                dict(k=257, alpha=0.05, beta=0.01)):
         with pytest.raises(pkg.SucoError) as e:
             pkg.suco_query_batch(ix, Qd, **kw)
@@ -266,7 +266,7 @@ def test_autotune_picks_a_shape_with_identical_results(tiny):
     Qd = torch.from_numpy(Q).to(dev)
     ref = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta, cluster_size=1, threads=512)
     cl, nt = pkg.suco_autotune(ix, Qd, w.k, w.alpha, w.beta)
-    assert cl in (1, 2, 4, 8, 16) and nt in (512, 1024)
+    assert cl in (1, 2, 4, 8, 16) and nt in (256, 512, 1024)
     got = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)
     torch.cuda.synchronize()
     assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])

@@ -1,7 +1,8 @@
-"""BF16 coarse re-rank vs the reduced-precision oracle, through the C ABI.
+"""BF16 and FP8 coarse re-rank vs the reduced-precision oracle, through the C ABI.
 
 The candidates come from the same bit-exact stages as the FP32 path; the coarse
-pass reads the BF16 copy of the dataset.  The survivors must be the R
+pass reads the BF16 copy of the dataset, or its FP8 E4M3 copy with one scale
+per subspace.  The survivors must be the R
 candidates with the smallest (coarse distance, id): the GPU sums in FP32, the
 oracle in FP64, so the two sets may differ only by candidates whose coarse
 distance ties the R-th one within FP32 rounding.  The final top-k must be the
@@ -46,12 +47,13 @@ def gpu_index(X, idx_o):
     return ix
 
 
-def check_bf16(X, idx_o, Q, k, alpha, beta, R, cluster_size=0, threads=0):
+def check_bf16(X, idx_o, Q, k, alpha, beta, R, cluster_size=0, threads=0, prec="bf16"):
     ix = gpu_index(X, idx_o)
+    scales = P.subspace_scales_e4m3(X, idx_o["Ns"]) if prec == "fp8" else None
     try:
         Qd = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
         out = pkg.suco_query_debug(ix, Qd, k, alpha, beta, cluster_size=cluster_size, threads=threads,
-                                   want=("cands", "survivors"), precision="bf16", exact_rerank=R)
+                                   want=("cands", "survivors"), precision=prec, exact_rerank=R)
         torch.cuda.synchronize()
         host = {kk: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for kk, v in out.items()}
     finally:
@@ -61,7 +63,8 @@ def check_bf16(X, idx_o, Q, k, alpha, beta, R, cluster_size=0, threads=0):
         o = oracle.query(X, idx_o, Q[b], k, T, C, rank_precision=1, debug=True)
         cands = o["cands"]
         assert sorted(host["cands"][b].tolist()) == sorted(cands.tolist())
-        ref = P.coarse_rerank(X, P.decoded_rows(X[cands], 1), Q[b], cands, R, k)
+        rows = P.decoded_rows(X[cands], 1) if prec == "bf16" else P.decoded_rows(X[cands], 2, idx_o["Ns"], scales)
+        ref = P.coarse_rerank(X, rows, Q[b], cands, R, k)
         g_surv = np.flatnonzero(host["survivors"][b])
         assert len(g_surv) == min(R, C) if C > R else True
         if C > R:
@@ -78,26 +81,29 @@ def check_bf16(X, idx_o, Q, k, alpha, beta, R, cluster_size=0, threads=0):
     return host
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
 @pytest.mark.parametrize("R", [10, 17, 32, 49])
-def test_bf16_survivors_and_topk(tiny, R):
+def test_coarse_survivors_and_topk(tiny, R, prec):
     w, X, Q, idx = tiny
-    check_bf16(X, idx, Q[:40], w.k, w.alpha, w.beta, R)
+    check_bf16(X, idx, Q[:40], w.k, w.alpha, w.beta, R, prec=prec)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
 @pytest.mark.parametrize("cluster_size", [1, 2, 4, 8, 16])
-@pytest.mark.parametrize("threads", [512, 1024])
-def test_bf16_every_launch_shape(tiny, cluster_size, threads):
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_coarse_every_launch_shape(tiny, cluster_size, threads, prec):
     w, X, Q, idx = tiny
-    check_bf16(X, idx, Q[:16], w.k, 0.1, 0.02, 37, cluster_size=cluster_size, threads=threads)
+    check_bf16(X, idx, Q[:16], w.k, 0.1, 0.02, 37, cluster_size=cluster_size, threads=threads, prec=prec)
 
 
-def test_bf16_with_all_candidates_surviving_equals_fp32(tiny):
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_coarse_with_all_candidates_surviving_equals_fp32(tiny, prec):
     w, X, Q, idx = tiny
     ix = gpu_index(X, idx)
     try:
         Qd = torch.from_numpy(Q).cuda()
         a = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta)
-        b = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta, precision="bf16", exact_rerank=50)
+        b = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta, precision=prec, exact_rerank=50)
         torch.cuda.synchronize()
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     finally:
@@ -123,17 +129,18 @@ def test_bf16_exact_on_integer_data():
         pkg.suco_free(ix)
 
 
-def test_bf16_ragged_dimension_and_ties():
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_coarse_ragged_dimension_and_ties(prec):
     # d = 13 (rows padded to 16 BF16 values), many duplicate points (coarse ties broken by id)
     rng = np.random.default_rng(7)
     base = rng.integers(0, 4, size=(300, 13)).astype(np.float32) * 0.37
     X = np.repeat(base, 7, axis=0)[rng.permutation(2100)]
     Q = (rng.integers(0, 4, size=(12, 13)).astype(np.float32) * 0.37 + rng.normal(0, 0.01, (12, 13))).astype(np.float32)
     idx = oracle.build_index(X, 3, 4, 3, W.random_init_ids(9, X.shape[0], 3, 4))
-    check_bf16(X, idx, Q, 5, 0.3, 0.1, 23)
+    check_bf16(X, idx, Q, 5, 0.3, 0.1, 23, prec=prec)
 
 
-def test_bf16_needs_the_copy(tiny):
+def test_reduced_precision_needs_its_copy(tiny):
     w, X, Q, idx = tiny
     Xd = torch.from_numpy(X).cuda()
     ix = pkg.suco_build_index_from_assignments(Xd, idx["Ns"], idx["sqrtK"], idx["centroids"], idx["assign"])
@@ -141,7 +148,22 @@ def test_bf16_needs_the_copy(tiny):
         with pytest.raises(pkg.SucoError) as e:
             pkg.suco_query_batch(ix, torch.from_numpy(Q).cuda(), w.k, w.alpha, w.beta, precision="bf16")
         assert e.value.code == -5
+        with pytest.raises(pkg.SucoError) as e:
+            pkg.suco_query_batch(ix, torch.from_numpy(Q).cuda(), w.k, w.alpha, w.beta, precision="fp8")
+        assert e.value.code == -5
         with pytest.raises(pkg.SucoError):
             pkg.suco_query_batch(ix, torch.from_numpy(Q).cuda(), w.k, w.alpha, w.beta, precision=7)
     finally:
         pkg.suco_free(ix)
+
+
+def test_fp8_codes_match_the_oracle_on_a_subspace_with_a_large_range():
+    # one subspace spans 1000x the range of the others: its own scale keeps its
+    # codes informative; the coarse pass still selects the oracle's survivors
+    rng = np.random.default_rng(9)
+    X = np.abs(rng.standard_normal((3000, 24))).astype(np.float32)
+    X[:, 16:] *= 1000.0
+    Q = np.abs(rng.standard_normal((16, 24))).astype(np.float32)
+    Q[:, 16:] *= 1000.0
+    idx = oracle.build_index(X, 3, 6, 3, W.random_init_ids(10, 3000, 3, 6))
+    check_bf16(X, idx, Q, 7, 0.2, 0.05, 31, prec="fp8")
