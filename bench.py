@@ -224,7 +224,7 @@ PLAIN_ALPHAS = (0.02, 0.05, 0.08, 0.12, 0.16, 0.2, 0.25, 0.3, 0.4)
 PLAIN_BETAS = (0.002, 0.005, 0.008, 0.012, 0.016, 0.024, 0.032)
 
 
-def time_loop(torch, stream, steps, warmup, fn, marks=1):
+def time_loop(torch, stream, steps, warmup, fn, marks=1, label=None):
     """Runs fn(s, ev) for warmup + steps steps; a timed step may record its
     internal marks ev[0 .. marks-2]; the step's start and end are recorded
     here.  Returns (total ms, per-step ms of each of the ``marks`` parts),
@@ -233,10 +233,14 @@ def time_loop(torch, stream, steps, warmup, fn, marks=1):
         fn(s, None)
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(marks + 1)] for _ in range(steps)]
+    if label:
+        torch.cuda.nvtx.range_push(label)  # lets a profiler select these launches (ncu --nvtx-include)
     for s in range(steps):
         ev[s][0].record(stream)
         fn(warmup + s, ev[s][1:marks])
         ev[s][marks].record(stream)
+    if label:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     total = ev[0][0].elapsed_time(ev[-1][-1])
     parts = [[ev[s][j].elapsed_time(ev[s][j + 1]) for j in range(marks)] for s in range(steps)]
@@ -344,7 +348,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     torch.cuda.synchronize()
     nq_step = [batches[order[s % nb]].shape[0] for s in range(args.steps)]
     with ClockSampler(local_rank) as clk:
-        total_ms, parts = time_loop(torch, stream, args.steps, args.warmup, learned_step, marks=2)
+        total_ms, parts = time_loop(torch, stream, args.steps, args.warmup, learned_step, marks=2, label="timed")
     if world > 1:
         tdist.barrier()
     torch.cuda.synchronize()
@@ -514,7 +518,7 @@ def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     torch.cuda.synchronize()
     nq_step = [batches[order[s % nb]].shape[0] for s in range(args.steps)]
     with ClockSampler(local_rank) as clk, torch.cuda.stream(stream):
-        total_ms, parts = time_loop(torch, stream, args.steps, args.warmup, step)
+        total_ms, parts = time_loop(torch, stream, args.steps, args.warmup, step, label="timed")
     if world > 1:
         tdist.barrier()
     torch.cuda.synchronize()
@@ -664,10 +668,12 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     nqueries = 0
     with ClockSampler(local_rank) as clk:
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
         ev[0].record(stream)
         for s in range(args.steps):
             nqueries += step(args.warmup + s)
             ev[s + 1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     if world > 1:
         tdist.barrier()

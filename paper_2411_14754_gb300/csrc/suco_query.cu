@@ -253,6 +253,55 @@ __device__ void block_bitonic_sort(unsigned long long* a, int P)
     }
 }
 
+__device__ __forceinline__ uint32_t next_pow2_dev(uint32_t x)
+{
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// One warp sorts keys[0, cnt) (cnt <= 32*S) ascending in place: a bitonic
+// network over element e = slot*32 + lane held in registers; strides of 32 and
+// more pair slots of the same lane, smaller strides pair lanes (shuffles).
+template <int S>
+__device__ __forceinline__ void warp_sort_keys(unsigned long long* keys, uint32_t cnt)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long v[S];
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) v[sl] = (uint32_t)(sl * 32 + lane) < cnt ? keys[sl * 32 + lane] : ~0ull;
+#pragma unroll
+    for (int size = 2; size <= 32 * S; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int ds = stride >> 5;
+#pragma unroll
+                for (int lo = 0; lo < S; ++lo) {
+                    if (lo & ds) continue;
+                    const int hi = lo | ds;
+                    const bool asc = ((lo * 32 + lane) & size) == 0;
+                    const unsigned long long x = v[lo], y = v[hi];
+                    if ((x > y) == asc) {
+                        v[lo] = y;
+                        v[hi] = x;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int sl = 0; sl < S; ++sl) {
+                    const int e = sl * 32 + lane;
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[sl], stride);
+                    const bool lower = (e & stride) == 0, asc = (e & size) == 0;
+                    if (lower == asc ? o < v[sl] : o > v[sl]) v[sl] = o;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) keys[sl * 32 + lane] = v[sl];
+}
+
 // Value bucket of a cell sum: monotone non-decreasing in s (FP32 subtract,
 // multiply and truncation are all monotone), so bucket order respects key order.
 __device__ __forceinline__ int value_bucket(float s, float smin, float scale)
@@ -1521,9 +1570,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     unsigned long long* best = keys;  // sorted top-k ends up here
     uint32_t nbest = 0;
     if (nk <= 2 * k || nk <= 64) {
-        for (uint32_t t = nk + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
-        __syncthreads();
-        block_bitonic_sort<NT>(keys, (int)A.sortP);
+        if (nk <= 128) {
+            if (warp == 0) warp_sort_keys<4>(keys, nk);
+            __syncthreads();
+        } else {
+            const uint32_t P = next_pow2_dev(nk);
+            for (uint32_t t = nk + threadIdx.x; t < P; t += NT) keys[t] = ~0ull;
+            __syncthreads();
+            block_bitonic_sort<NT>(keys, (int)P);
+        }
         nbest = min(k, nk);
     } else {
         if (threadIdx.x == 0) {
@@ -1586,36 +1641,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             }
             __syncthreads();
             if (ns <= 64) {
-                // one warp sorts up to 64 keys in registers (bitonic network over
-                // element e = slot*32 + lane; stride 32 pairs the two slots of a lane)
-                if (warp == 0) {
-                    unsigned long long v[2];
-                    v[0] = (uint32_t)lane < ns ? surv[lane] : ~0ull;
-                    v[1] = (uint32_t)lane + 32 < ns ? surv[lane + 32] : ~0ull;
-#pragma unroll
-                    for (int size = 2; size <= 64; size <<= 1) {
-#pragma unroll
-                        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                            if (stride == 32) {
-                                if (v[0] > v[1]) {  // size 64: ascending, slot 0 is the lower element
-                                    const unsigned long long t = v[0];
-                                    v[0] = v[1];
-                                    v[1] = t;
-                                }
-                            } else {
-#pragma unroll
-                                for (int sl = 0; sl < 2; ++sl) {
-                                    const int e = sl * 32 + lane;
-                                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[sl], stride);
-                                    const bool lower = (e & stride) == 0, asc = (e & size) == 0;
-                                    if (lower == asc ? o < v[sl] : o > v[sl]) v[sl] = o;
-                                }
-                            }
-                        }
-                    }
-                    surv[lane] = v[0];
-                    surv[lane + 32] = v[1];
-                }
+                if (warp == 0) warp_sort_keys<2>(surv, ns);
+                __syncthreads();
+            } else if (ns <= 128) {
+                if (warp == 0) warp_sort_keys<4>(surv, ns);
                 __syncthreads();
             } else {
                 uint32_t P = 1;
@@ -1628,9 +1657,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             nbest = min(k, ns);
         } else {
             // a crowded bucket (many equal distances): sort the whole share
-            for (uint32_t t = nk + threadIdx.x; t < A.sortP; t += NT) keys[t] = ~0ull;
+            const uint32_t P = next_pow2_dev(nk);
+            for (uint32_t t = nk + threadIdx.x; t < P; t += NT) keys[t] = ~0ull;
             __syncthreads();
-            block_bitonic_sort<NT>(keys, (int)A.sortP);
+            block_bitonic_sort<NT>(keys, (int)P);
             nbest = min(k, nk);
         }
     }
@@ -1759,7 +1789,8 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     A.run_stride = (A.per_cta + 15) & ~15u;
     A.o_run = (uint32_t)o;
     if (npass > 1) o = align16(o + 10ull * A.run_stride);
-    A.sortP = next_pow2(std::max<uint32_t>(A.per_cta, 1));
+    // at least 128: the warp sort of a small share writes 128 keys back
+    A.sortP = next_pow2(std::max<uint32_t>(A.per_cta, 128));
     A.o_union = (uint32_t)o;
     A.nbits = nsmax == 8 ? 4 : (nsmax == 16 ? 5 : 6);
     // S4 counters: nibble sets of up to 15 subspaces, then one-bit planes for
