@@ -35,6 +35,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2411_14754_gb300 import replicas as R  # noqa: E402 (which batches a rank answers, timing reduction)
+
 METRIC = "QPS at recall@10>=0.95 on 1 GB300, learned-alpha/BF16 vs plain FP32; % HBM peak"
 UNIT = "queries/s"
 
@@ -284,7 +286,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     B = w.batch
     nb = (w.nq + B - 1) // B
     batches = [Qe[i * B:(i + 1) * B] for i in range(nb)]
-    order = [(rank + i * world) % nb for i in range(nb)]
+    order = R.batch_order(rank, world, nb)
     outs = [(torch.empty((b.shape[0], w.k), dtype=torch.int32, device=dev),
              torch.empty((b.shape[0], w.k), dtype=torch.float32, device=dev)) for b in batches]
     ab = [(torch.empty(b.shape[0], device=dev), torch.empty(b.shape[0], device=dev)) for b in batches]
@@ -353,14 +355,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
         tdist.barrier()
     torch.cuda.synchronize()
     nqueries = float(sum(nq_step))
-    tot = torch.tensor([total_ms, nqueries], dtype=torch.float64, device=dev)
-    if world > 1:
-        mx, sm = tot.clone(), tot.clone()
-        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
-        total_ms, all_q = float(mx[0]), float(sm[1])
-    else:
-        all_q = nqueries
+    total_ms, all_q = R.reduce_throughput(tdist, dev, total_ms, nqueries, world)
     value = all_q / (total_ms / 1000.0)
     predict_ms = statistics.mean(p[0] for p in parts)
     query_ms = statistics.mean(p[1] for p in parts)
@@ -391,13 +386,8 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
         bi = order[(args.warmup + s) % nb]
         h2d += hq[bi].numel() * 4
         d2h += hout[bi][0].numel() * 4 + hout[bi][1].numel() * 4
-    e2e_value = sum(nq_step) / (e2e_ms / 1000.0)
-    if world > 1:
-        t = torch.tensor([e2e_ms, float(sum(nq_step))], dtype=torch.float64, device=dev)
-        mx, sm = t.clone(), t.clone()
-        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
-        e2e_value = float(sm[1]) / (float(mx[0]) / 1000.0)
+    e_ms, e_q = R.reduce_throughput(tdist, dev, e2e_ms, float(sum(nq_step)), world)
+    e2e_value = e_q / (e_ms / 1000.0)
 
     # roofline of the query kernel: per query 4 * sum_i T_eff,i id bytes and
     # 4 * C_b * d row bytes, C_b from the query's own beta (with the BF16
@@ -486,7 +476,7 @@ def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     aq = [torch.from_numpy(als[c].astype(np.float32)).to(dev) for c in sl]
     outs = [(torch.empty((b.shape[0], kmax), dtype=torch.int32, device=dev),
              torch.empty((b.shape[0], kmax), dtype=torch.float32, device=dev)) for b in batches]
-    order = [(rank + i * world) % nb for i in range(nb)]
+    order = R.batch_order(rank, world, nb)
     amax = float(max(w.alpha_mix))
     shape = pkg.suco_autotune(index, batches[0], kmax, amax, w.beta, k_per_query=kq[0], alpha_per_query=aq[0])
     note(f"autotuned launch shape (cluster size, threads): {shape}")
@@ -522,14 +512,7 @@ def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     if world > 1:
         tdist.barrier()
     torch.cuda.synchronize()
-    tot = torch.tensor([total_ms, float(sum(nq_step))], dtype=torch.float64, device=dev)
-    if world > 1:
-        mx, sm = tot.clone(), tot.clone()
-        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
-        total_ms, all_q = float(mx[0]), float(sm[1])
-    else:
-        all_q = float(sum(nq_step))
+    total_ms, all_q = R.reduce_throughput(tdist, dev, total_ms, float(sum(nq_step)), world)
     value = all_q / (total_ms / 1000.0)
     mean_launch_ms = total_ms / args.steps
 
@@ -556,7 +539,8 @@ def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
         bi = order[(args.warmup + s) % nb]
         h2d += hq[bi].numel() * 4 + hk[bi].numel() * 4 + ha[bi].numel() * 4
         d2h += hout[bi][0].numel() * 4 + hout[bi][1].numel() * 4
-    e2e_value = sum(nq_step) / (e2e_ms / 1000.0)
+    e_ms, e_q = R.reduce_throughput(tdist, dev, e2e_ms, float(sum(nq_step)), world)
+    e2e_value = e_q / (e_ms / 1000.0)
 
     # recall@k_b of a sample of queries against exact k-NN, and T_eff for the roofline
     from paper_2411_14754_gb300 import learn as L
@@ -648,7 +632,7 @@ def main():
     nb = (w.nq + B - 1) // B
     # every rank answers different batches (query-sharded replicas)
     batches = [torch.from_numpy(Qall[i * B:(i + 1) * B]).to(dev) for i in range(nb)]
-    order = [(rank + i * world) % nb for i in range(nb)]
+    order = R.batch_order(rank, world, nb)
     stream = torch.cuda.current_stream(dev)
     outs = [(torch.empty((b.shape[0], w.k), dtype=torch.int32, device=dev),
              torch.empty((b.shape[0], w.k), dtype=torch.float32, device=dev)) for b in batches]
@@ -681,15 +665,7 @@ def main():
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[args.steps])
     # slowest rank decides; queries are summed over ranks
-    tot = torch.tensor([total_ms, float(nqueries)], dtype=torch.float64, device=dev)
-    if world > 1:
-        mx = tot.clone()
-        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-        sm = tot.clone()
-        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
-        total_ms, all_queries = float(mx[0]), float(sm[1])
-    else:
-        all_queries = float(nqueries)
+    total_ms, all_queries = R.reduce_throughput(tdist, dev, total_ms, float(nqueries), world)
     value = all_queries / (total_ms / 1000.0)
 
     # end to end through the public API: pinned host queries in, host results out, every step
@@ -722,14 +698,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    e2e_value = eq / (e2e_ms / 1000.0)
-    if world > 1:
-        t = torch.tensor([e2e_ms, float(eq)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-        sm = t.clone()
-        tdist.all_reduce(sm, op=tdist.ReduceOp.SUM)
-        e2e_value = float(sm[1]) / (float(mx[0]) / 1000.0)
+    e_ms, e_q = R.reduce_throughput(tdist, dev, e2e_ms, float(eq), world)
+    e2e_value = e_q / (e_ms / 1000.0)
 
     # recall@k against exact k-NN (GPU brute force shortlist, FP64 re-check), and T_eff for the roofline
     from oracle import recall as _recall
