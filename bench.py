@@ -415,7 +415,8 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     hbm = hbm or 6800.0
     achieved = bytes_steps / args.steps / (query_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": committed_traffic(w.number), "peak_source": peak_src,
+                "traffic": committed_traffic(f"{w.number}-learned") if learned_prec == "fp32" else None,
+                "peak_source": peak_src,
                 "kernel": f"suco_query_kernel (learned per-query alpha/beta, {learned_prec} re-rank, one launch per batch)",
                 "algorithmic_bytes_per_query": bytes_steps / sum(nq_step), "mean_launch_ms": query_ms}
 
@@ -735,7 +736,8 @@ def main():
         bpq = 4.0 * teff_total + (eb * Cc + 4.0 * args.exact_rerank) * w.d
     mean_launch_ms = statistics.mean(step_ms)
     achieved = bpq * B / (mean_launch_ms / 1000.0) / 1e9
-    traffic = committed_traffic(w.number)
+    # the committed capture is of the FP32 path; another precision has none
+    traffic = committed_traffic(w.number) if args.precision == "fp32" and args.rank_precision == "fp32" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_source": peak_src,
                 "kernel": "suco_query_kernel (whole query path, one launch per batch)",
