@@ -58,8 +58,12 @@ def exact_knn(Xd: torch.Tensor, Qd: torch.Tensor, k: int, shortlist: int = 1000,
 
 
 def recall_rows(ids: np.ndarray, gt: np.ndarray) -> np.ndarray:
+    """|ids_b intersect gt_b| / k per row (ids within a row are distinct)."""
+    ids = np.asarray(ids)
+    gt = np.asarray(gt)
     k = gt.shape[1]
-    return np.array([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt)])
+    hit = (ids[:, :, None] == gt[:, None, :]) & (gt[:, None, :] >= 0)
+    return hit.any(axis=2).sum(axis=1) / k
 
 
 def path_bytes(alpha, beta, n, d, Ns):
@@ -242,6 +246,27 @@ def tune_offsets(index, model, Qd, gt, k, target=0.95, grid=np.arange(-1.0, 2.51
         if r >= target:
             return float(m), r
     return float(grid[-1]), r
+
+
+def margin_grid(index, model, Qd, gt, k, target=0.95, grid=np.arange(-0.5, 2.01, 0.25), **kw):
+    """Separate margins for log alpha and log beta: for every pair (ma, mb) of
+    the grid, the mean recall@k on (Qd, gt) and the mean modelled path bytes
+    of the predicted ratios.  Returns the pairs reaching the target as
+    (bytes, ma, mb, recall), cheapest first."""
+    out = []
+    for ma in grid:
+        for mb in grid:
+            alpha, beta = predict(index, model, Qd, offsets=(ma, mb))
+            ids, _ = S.suco_query_batch(index, Qd, k, FALLBACK[0], BETA_RANGE[1], alpha_per_query=alpha,
+                                        beta_per_query=beta, **kw)
+            r = float(recall_rows(ids.cpu().numpy(), gt).mean())
+            if r >= target:
+                a_np = alpha.cpu().numpy().astype(np.float64)
+                b_np = np.minimum(beta.cpu().numpy().astype(np.float64), BETA_RANGE[1])
+                cost = float(np.mean(path_bytes(a_np, b_np, index.n, index.d, index.Ns)))
+                out.append((cost, float(ma), float(mb), r))
+    out.sort()
+    return out
 
 
 def cheapest_fixed(rec_mean, n, d, Ns, target=0.95, alphas=ALPHA_GRID, betas=BETA_GRID):
