@@ -121,7 +121,7 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
         {(void**)&ix->X, (size_t)n * ix->ld * 4},
         {(void**)&ix->cent, (size_t)Ns * 2 * sqrtK * ix->hmax * 4},
         {(void**)&ix->cell_off, (size_t)Ns * (ix->K + 1) * 4},
-        {(void**)&ix->perm, (size_t)Ns * n * 4},
+        {(void**)&ix->perm, (size_t)Ns * n * 4 + 16},  // padded: the query scan reads whole 16-byte quads
         {(void**)&ix->split, (size_t)Ns * (ix->nch + 1) * ix->K * 4},
         {(void**)&ix->work, (size_t)(STATUS_WORD + WORK_STRIDE) * 4},
     };

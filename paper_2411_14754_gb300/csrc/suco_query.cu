@@ -51,10 +51,10 @@
 namespace suco {
 namespace {
 
-constexpr int MAXSEG = 1024;  // retrieved-cell segments listed per scan round
+constexpr int MAXSEG = 512;   // retrieved-cell segments listed per scan round
 constexpr int NB = 1024;      // linear value buckets of the cut search
 constexpr int MCAP = 1024;    // cells of the crossing bucket resolved from a list
-constexpr int SCAN_U = 8;     // ids in flight per lane in the scan
+constexpr int SCAN_U = 4;     // 16-byte quads of ids in flight per lane in the scan
 
 constexpr int S3_BYTES = 4 * NB + 12 * MCAP;  // S3 scratch at the start of the union region
 constexpr int SURV_CAP = 512; // keys kept for the final sort of a local top-k
@@ -658,19 +658,22 @@ template <int NT>
 __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t m, const uint32_t* sub_pre,
                               const uint32_t* sub_wb, uint32_t* cnt_words, uint32_t id0, int j0, int j1)
 {
-    // the non-empty segments in flat order: (perm index of the first id minus
-    // the flat start, counter word base | nibble flag), and their flat starts
-    uint2* seg_info = reinterpret_cast<uint2*>(smem + A.o_seg);   // [MAXSEG]
+    // the non-empty segments in flat order, counted in 16-byte quads of the id
+    // lists (perm): {quad index of the first quad minus the flat start, perm
+    // position of the first id, perm position past the last id, counter word
+    // base | nibble flag}, and their flat starts
+    uint4* seg_info = reinterpret_cast<uint4*>(smem + A.o_seg);          // [MAXSEG]
     uint32_t* seg_pre = reinterpret_cast<uint32_t*>(seg_info + MAXSEG);  // [MAXSEG+1]
     uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
     const int sk = A.sqrtK;
-    constexpr int EPT = MAXSEG / NT;
-    uint32_t len[EPT], pbase[EPT], mode[EPT], s = 0, ne = 0;
+    constexpr int EPT = (MAXSEG + NT - 1) / NT;
+    uint32_t nqd[EPT], pP[EPT], pE[EPT], mode[EPT], s = 0, ne = 0;
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
         const uint32_t e = threadIdx.x * EPT + u;
-        len[u] = 0;
-        pbase[u] = 0;
+        nqd[u] = 0;
+        pP[u] = 0;
+        pE[u] = 0;
         mode[u] = 0;
         if (e < m) {
             const uint32_t g = e0 + e;
@@ -688,37 +691,40 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
             const uint32_t* sp = A.split + (int64_t)i * (A.nch + 1) * A.K + cell;
             const uint32_t s0 = __ldg(sp + (int64_t)j0 * A.K);
             const uint32_t s1 = __ldg(sp + (int64_t)j1 * A.K);
-            len[u] = s1 - s0;
-            pbase[u] = (uint32_t)i * (uint32_t)A.n + s0;
+            pP[u] = (uint32_t)i * (uint32_t)A.n + s0;
+            pE[u] = (uint32_t)i * (uint32_t)A.n + s1;
+            nqd[u] = s1 > s0 ? ((pE[u] + 3u) >> 2) - (pP[u] >> 2) : 0u;
             mode[u] = sub_wb[i];
         }
-        s += len[u];
-        ne += len[u] ? 1u : 0u;
+        s += nqd[u];
+        ne += nqd[u] ? 1u : 0u;
     }
     uint32_t F, M;
     uint32_t run = block_exclusive_scan<NT>(s, wtmp, &F);
     uint32_t slot = block_exclusive_scan<NT>(ne, wtmp, &M);
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
-        if (len[u]) {
+        if (nqd[u]) {
             seg_pre[slot] = run;
-            seg_info[slot] = make_uint2(pbase[u] - run, mode[u]);  // perm index = .x + flat position (mod 2^32)
+            seg_info[slot] = make_uint4((pP[u] >> 2) - run, pP[u], pE[u], mode[u]);  // quad = .x + flat position
             ++slot;
         }
-        run += len[u];
+        run += nqd[u];
     }
     if (threadIdx.x == 0) seg_pre[M] = F;
     __syncthreads();
-    // each warp takes a contiguous share [wb, we) of the F ids in windows of 32
-    // consecutive positions (one per lane); the warp holds the starts of the
-    // next 32 segments in its lanes, so a lane finds the segment of its
-    // position with a ballot and a population count instead of a walk
+    // each warp takes a contiguous share [wb, we) of the F quads in windows of
+    // 32 consecutive quads (one per lane); the warp holds the starts of the
+    // next 32 segments in its lanes, so a lane finds the segment of its quad
+    // with a ballot and a population count; it loads the quad's 4 ids with one
+    // 16-byte load and keeps those inside the segment's perm range
     constexpr int NW = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t share = (F + NW - 1) / NW;
     const uint32_t wb = min(F, (uint32_t)warp * share), we = min(F, wb + share);
     uint32_t lanemask_le;
     asm("mov.u32 %0, %%lanemask_le;" : "=r"(lanemask_le));
+    const uint4* perm4 = reinterpret_cast<const uint4*>(A.perm);
     if (wb < we) {
         int lo = 0, hi = (int)M - 1;  // the segment holding wb
         while (lo < hi) {
@@ -732,30 +738,40 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
             const uint32_t Bj = sj <= M ? seg_pre[sj] : 0xffffffffu;  // start of segment sg0+1+lane
             const uint32_t B31 = __shfl_sync(0xffffffffu, Bj, 31);
             const uint32_t wend = min(we, min(w0 + 32u * SCAN_U, B31));  // segments sg0 .. sg0+31 only
-            int32_t idv[SCAN_U];
-            uint32_t md[SCAN_U];
+            uint4 q[SCAN_U];
+            uint32_t vmask[SCAN_U], md[SCAN_U];  // ids of the quad inside the segment (bit j: element j)
 #pragma unroll
             for (int u = 0; u < SCAN_U; ++u) {
                 const uint32_t x = w0 + 32u * (uint32_t)u, pu = x + (uint32_t)lane;
                 const uint32_t before = __popc(__ballot_sync(0xffffffffu, Bj <= x));
                 const uint32_t o = Bj - x;  // segment starts strictly inside the window
                 const uint32_t mk = __reduce_or_sync(0xffffffffu, o - 1u < 31u ? 1u << o : 0u);
-                idv[u] = -1;
+                q[u] = make_uint4(0u, 0u, 0u, 0u);
+                vmask[u] = 0u;
                 md[u] = 0u;
                 if (pu < wend) {
-                    const uint2 inf = seg_info[sg0 + before + __popc(mk & lanemask_le)];
-                    md[u] = inf.y;
-                    idv[u] = __ldg(A.perm + (uint32_t)(inf.x + pu));
+                    const uint4 inf = seg_info[sg0 + before + __popc(mk & lanemask_le)];
+                    const uint32_t qi = inf.x + pu, p0 = qi << 2;
+                    // the quad overlaps the segment's perm range [inf.y, inf.z)
+                    const uint32_t lo = inf.y > p0 ? inf.y - p0 : 0u, hi = min(inf.z - p0, 4u);
+                    vmask[u] = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+                    md[u] = inf.w;
+                    q[u] = __ldg(perm4 + qi);
                 }
             }
 #pragma unroll
             for (int u = 0; u < SCAN_U; ++u) {
-                const uint32_t loc = (uint32_t)idv[u] - id0;
-                if (idv[u] >= 0 && loc < span) {
-                    const uint32_t t = loc & 31u;
-                    const bool nib = (md[u] >> 31) != 0u;
-                    const uint32_t w = (md[u] & 0x7fffffffu) + (nib ? (t & 3u) * G : 0u) + (loc >> 5);
-                    atomicAdd(&cnt_words[w], 1u << (nib ? (t & 28u) : t));
+                const uint32_t idq[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+                const bool nib = (md[u] >> 31) != 0u;
+                const uint32_t wbase = md[u] & 0x7fffffffu;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t loc = idq[j] - id0;
+                    if (((vmask[u] >> j) & 1u) && loc < span) {
+                        const uint32_t t = loc & 31u;
+                        const uint32_t w = wbase + (nib ? (t & 3u) * G : 0u) + (loc >> 5);
+                        atomicAdd(&cnt_words[w], 1u << (nib ? (t & 28u) : t));
+                    }
                 }
             }
             sg0 += __popc(__ballot_sync(0xffffffffu, Bj <= wend));
@@ -1783,7 +1799,7 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     // followed by this CTA's candidate slots
     A.o_seg = (uint32_t)o;
     A.o_slots = (uint32_t)(o + align16(8ull * CL * k));
-    o = align16(o + std::max<uint64_t>(8ull * MAXSEG + 4ull * (MAXSEG + 1), align16(8ull * CL * k) + 4ull * A.per_cta));
+    o = align16(o + std::max<uint64_t>(16ull * MAXSEG + 4ull * (MAXSEG + 1), align16(8ull * CL * k) + 4ull * A.per_cta));
     // a multi-pass query's running candidate list lives across the passes'
     // S4 (which reuses the segment region), so it has a region of its own
     A.run_stride = (A.per_cta + 15) & ~15u;
