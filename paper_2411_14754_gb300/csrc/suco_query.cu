@@ -149,6 +149,16 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr)
     return v;
 }
 
+__device__ __forceinline__ uint4 ld_cluster_v4(uint32_t addr)
+{
+    uint4 v;
+    asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v)
 {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
@@ -264,12 +274,9 @@ __device__ __forceinline__ uint32_t next_pow2_dev(uint32_t x)
 // network over element e = slot*32 + lane held in registers; strides of 32 and
 // more pair slots of the same lane, smaller strides pair lanes (shuffles).
 template <int S>
-__device__ __forceinline__ void warp_sort_keys(unsigned long long* keys, uint32_t cnt)
+__device__ __forceinline__ void warp_sort_regs(unsigned long long (&v)[S])
 {
     const int lane = threadIdx.x & 31;
-    unsigned long long v[S];
-#pragma unroll
-    for (int sl = 0; sl < S; ++sl) v[sl] = (uint32_t)(sl * 32 + lane) < cnt ? keys[sl * 32 + lane] : ~0ull;
 #pragma unroll
     for (int size = 2; size <= 32 * S; size <<= 1) {
 #pragma unroll
@@ -298,6 +305,16 @@ __device__ __forceinline__ void warp_sort_keys(unsigned long long* keys, uint32_
             }
         }
     }
+}
+
+template <int S>
+__device__ __forceinline__ void warp_sort_keys(unsigned long long* keys, uint32_t cnt)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long v[S];
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) v[sl] = (uint32_t)(sl * 32 + lane) < cnt ? keys[sl * 32 + lane] : ~0ull;
+    warp_sort_regs<S>(v);
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) keys[sl * 32 + lane] = v[sl];
 }
@@ -677,8 +694,11 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
         mode[u] = 0;
         if (e < m) {
             const uint32_t g = e0 + e;
-            int i = 0;
-            while (sub_pre[i + 1] <= g) ++i;
+            int i = 0, ihi = A.Ns - 1;  // the last subspace whose list starts at or before g
+            while (i < ihi) {
+                const int mid = (i + ihi + 1) >> 1;
+                if (sub_pre[mid] <= g) i = mid; else ihi = mid - 1;
+            }
             Tab tb = tab_at(smem, A, i);
             const uint32_t rl = g - sub_pre[i];
             int lo = 0, hi = sk - 1;  // last ranked row with row_pre <= rl
@@ -1241,15 +1261,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     if (A.work && r == 0 && threadIdx.x == 0)
         for (int t = 0; t < CL; ++t) st_cluster_u32(map_rank(smem_addr(next_q), (uint32_t)t), grabbed);
 
-    // ---- copy the other CTAs' tables
+    // ---- copy the other CTAs' tables (16-byte loads: the stride is a multiple of 16)
     {
-        const uint32_t words = A.tab_stride / 4;
-        for (uint32_t t = threadIdx.x; t < (uint32_t)A.Ns * words; t += NT) {
-            const int i = t / words;
+        const uint32_t vecs = A.tab_stride / 16;
+        for (uint32_t t = threadIdx.x; t < (uint32_t)A.Ns * vecs; t += NT) {
+            const int i = t / vecs;
             const uint32_t owner = (uint32_t)(i % CL);
             if (owner == r) continue;
-            uint32_t* dst = reinterpret_cast<uint32_t*>(smem + A.o_tab + (size_t)i * A.tab_stride) + (t - i * words);
-            *dst = ld_cluster_u32(map_rank(smem_addr(dst), owner));
+            uint4* dst = reinterpret_cast<uint4*>(smem + A.o_tab + (size_t)i * A.tab_stride) + (t - i * vecs);
+            *dst = ld_cluster_v4(map_rank(smem_addr(dst), owner));
         }
     }
     __syncthreads();
