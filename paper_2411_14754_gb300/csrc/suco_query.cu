@@ -109,6 +109,7 @@ struct QArgs {
     uint32_t o_tab, tab_stride, o_q, o_hist, o_misc, o_cnt, o_seg, o_slots, o_keys, o_union;
     uint32_t sortP;       // power of two >= the CTA's candidate share (fallback sort)
     uint32_t stage_cent;  // 1: the subspace's centroids are staged in shared memory
+    uint32_t o_cells;     // nonzero: the subspace's cell offsets are copied to o_union + o_cells for S3
 };
 
 // ---------------------------------------------------------------------------
@@ -165,6 +166,14 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v)
 }
 
 // 16-byte global load that bypasses L1 (candidate rows are read once)
+// asynchronous 4-byte global -> shared copy (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ float4 ldg_stream(const float4* p)
 {
     float4 v;
@@ -263,6 +272,45 @@ __device__ void block_bitonic_sort(unsigned long long* a, int P)
     }
 }
 
+// Slot of this lane among the lanes of its warp with pred set, after one
+// atomicAdd of their number on *ctr (a warp's lanes would otherwise queue on
+// the same shared word one by one).  Every lane of the warp calls it.
+__device__ __forceinline__ uint32_t warp_alloc(uint32_t* ctr, bool pred)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t m = __ballot_sync(0xffffffffu, pred);
+    const int leader = m ? __ffs(m) - 1 : 0;
+    uint32_t base = 0u;
+    if (m && lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+}
+
+// Number of keys smaller than v over CLT sorted lists of k keys each
+// (all + o*k), by CLT binary searches taken in lock step: every step issues
+// one unconditional (clamped) load per list, so a step costs one shared-memory
+// round trip instead of CLT dependent ones.  P is a power of two with P > k.
+// v's own list contributes v's position in it (keys are unique).
+template <int CLT>
+__device__ __forceinline__ uint32_t rank_in_lists(const unsigned long long* all, uint32_t k, uint32_t P,
+                                                  unsigned long long v)
+{
+    uint32_t pos[CLT];
+#pragma unroll
+    for (int o = 0; o < CLT; ++o) pos[o] = 0u;
+    for (uint32_t st = P >> 1; st; st >>= 1) {
+        unsigned long long x[CLT];
+#pragma unroll
+        for (int o = 0; o < CLT; ++o) x[o] = all[(uint32_t)o * k + min(pos[o] + st, k) - 1u];
+#pragma unroll
+        for (int o = 0; o < CLT; ++o) pos[o] = (pos[o] + st <= k && x[o] < v) ? pos[o] + st : pos[o];
+    }
+    uint32_t rank = 0u;
+#pragma unroll
+    for (int o = 0; o < CLT; ++o) rank += pos[o];
+    return rank;
+}
+
 __device__ __forceinline__ uint32_t next_pow2_dev(uint32_t x)
 {
     uint32_t p = 1;
@@ -339,6 +387,12 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     const int soff = i * A.sub_s;
     const int slen = (i == A.Ns - 1) ? A.d - (A.Ns - 1) * A.sub_s : A.sub_s;
     const int first = slen / 2;
+    // the subspace's cell offsets (the index's cell sizes) are copied to shared
+    // memory while S1 and S2 run; S3 reads each of them up to twice
+    const uint32_t* co = A.cell_off + (int64_t)i * (A.K + 1);
+    uint32_t* co_s = A.o_cells ? reinterpret_cast<uint32_t*>(smem + A.o_union + A.o_cells) : nullptr;
+    if (co_s)
+        for (int t = threadIdx.x; t <= A.K; t += NT) cp_async4(co_s + t, co + t);
     // S1: squared distances to the 2*sqrtK half-subspace centroids.  The
     // subspace's centroids are staged dimension-major ([h][j][a]) so that
     // consecutive threads read consecutive words.
@@ -402,7 +456,9 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     uint32_t* h256 = reinterpret_cast<uint32_t*>(smem + A.o_hist);
     unsigned long long* bc = reinterpret_cast<unsigned long long*>(smem + A.o_misc);
     uint32_t* mcount = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 14;
-    const uint32_t* co = A.cell_off + (int64_t)i * (A.K + 1);
+    auto cell_size = [&](uint32_t x) -> uint32_t {
+        return co_s ? co_s[x + 1] - co_s[x] : __ldg(co + x + 1) - __ldg(co + x);
+    };
     const float smin = __fadd_rn(tb.d1[tb.idx1[0]], tb.d2[tb.idx2[0]]);
     const float smax = __fadd_rn(tb.d1[tb.idx1[sk - 1]], tb.d2[tb.idx2[sk - 1]]);
     const float range = __fsub_rn(smax, smin);
@@ -416,12 +472,13 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
 
     for (int t = threadIdx.x; t < NB; t += NT) hist[t] = 0u;
     if (threadIdx.x == 0) *mcount = 0u;
+    if (co_s) cp_async_wait_all();
     __syncthreads();
     if (c_of < sk) {
         const float d2c = tb.d2[c_of];
         for (int a = a_of; a < sk; a += a_step) {
             const uint32_t x = (uint32_t)(a * sk + c_of);
-            const uint32_t w = __ldg(co + x + 1) - __ldg(co + x);
+            const uint32_t w = cell_size(x);
             if (w) atomicAdd(&hist[value_bucket(__fadd_rn(tb.d1[a], d2c), smin, scale)], w);
         }
     }
@@ -459,7 +516,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
             const float s = __fadd_rn(tb.d1[a], d2c);
             if (value_bucket(s, smin, scale) != bstar) continue;
             const uint32_t x = (uint32_t)(a * sk + c_of);
-            const uint32_t w = __ldg(co + x + 1) - __ldg(co + x);
+            const uint32_t w = cell_size(x);
             if (!w) continue;
             const uint32_t slot = atomicAdd(mcount, 1u);
             if (slot < MCAP) {
@@ -559,7 +616,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
                     ((unsigned long long)__float_as_uint(s) << 16) | ((uint32_t)tb.r1[a] << 8) | r2c;
                 if ((key & mask) != prefix) continue;
                 const uint32_t x = (uint32_t)(a * sk + c_of);
-                const uint32_t w = __ldg(co + x + 1) - __ldg(co + x);
+                const uint32_t w = cell_size(x);
                 if (w) atomicAdd(&h256[(key >> shift) & 255u], w);
             }
         }
@@ -1582,11 +1639,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         if (threadIdx.x == 0) *ns = 0u;
         __syncthreads();
         uint32_t* surv_ids = const_cast<uint32_t*>(slots);  // the candidate ids now live in the keys
-        for (uint32_t t = threadIdx.x; t < mine; t += NT) {
-            const unsigned long long key = keys[t];
-            if (key <= cut) {
+        for (uint32_t t0 = 0; t0 < mine; t0 += NT) {  // CTA-uniform trip count: warp_alloc needs whole warps
+            const uint32_t t = t0 + threadIdx.x;
+            const unsigned long long key = t < mine ? keys[t] : ~0ull;
+            const bool keep = t < mine && key <= cut;
+            const uint32_t slot = warp_alloc(ns, keep);
+            if (keep) {
                 const uint32_t id = (uint32_t)(key & 0xffffffffu);
-                surv_ids[atomicAdd(ns, 1u)] = id;
+                surv_ids[slot] = id;
                 if (A.dbg_surv) A.dbg_surv[b * A.n + id] = 1u;
             }
         }
@@ -1632,8 +1692,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             lo = min(lo, db);
             hi = max(hi, db);
         }
-        if (lo != 0xffffffffu) atomicMin(&kv[0], lo);
-        if (hi) atomicMax(&kv[1], hi);
+        lo = __reduce_min_sync(0xffffffffu, lo);  // one atomic per warp
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0 && lo != 0xffffffffu) atomicMin(&kv[0], lo);
+        if (lane == 0 && hi) atomicMax(&kv[1], hi);
         __syncthreads();
         const float dmin = __uint_as_float(kv[0]);
         const float drange = __fsub_rn(__uint_as_float(kv[1]), dmin);
@@ -1670,10 +1732,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             uint32_t* ctr = kv + 4;
             if (threadIdx.x == 0) *ctr = 0u;
             __syncthreads();
-            for (uint32_t t = threadIdx.x; t < nk; t += NT) {
-                const unsigned long long v = keys[t];
-                if (v != ~0ull && (uint32_t)value_bucket(__uint_as_float((uint32_t)(v >> 32)), dmin, dscale) <= kb)
-                    surv[atomicAdd(ctr, 1u)] = v;
+            for (uint32_t t0 = 0; t0 < nk; t0 += NT) {  // CTA-uniform trip count: warp_alloc needs whole warps
+                const uint32_t t = t0 + threadIdx.x;
+                const unsigned long long v = t < nk ? keys[t] : ~0ull;
+                const bool keep =
+                    v != ~0ull && (uint32_t)value_bucket(__uint_as_float((uint32_t)(v >> 32)), dmin, dscale) <= kb;
+                const uint32_t slot = warp_alloc(ctr, keep);
+                if (keep) surv[slot] = v;
             }
             __syncthreads();
             if (ns <= 64) {
@@ -1721,28 +1786,27 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         if (threadIdx.x == 0) *nreal = 0u;
         __syncthreads();
         uint32_t real = 0;
+        uint32_t P = 2;  // a power of two above k
+        while (P <= k) P <<= 1;
         for (uint32_t t = threadIdx.x; t < tot; t += NT) {
             const unsigned long long v = all[t];
             if (v == ~0ull) continue;
             ++real;
-            const uint32_t rr = t / k;
-            uint32_t rank = t - rr * k;
-            for (int o = 0; o < CL && rank < k; ++o) {
-                if (o == (int)rr) continue;
-                const unsigned long long* lst = all + (size_t)o * k;
-                uint32_t lo = 0, hi = k;  // keys < v in list o
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (lst[mid] < v) lo = mid + 1; else hi = mid;
-                }
-                rank += lo;
+            uint32_t rank;
+            switch (CL) {
+                case 16: rank = rank_in_lists<16>(all, k, P, v); break;
+                case 8: rank = rank_in_lists<8>(all, k, P, v); break;
+                case 4: rank = rank_in_lists<4>(all, k, P, v); break;
+                case 2: rank = rank_in_lists<2>(all, k, P, v); break;
+                default: rank = rank_in_lists<1>(all, k, P, v); break;
             }
             if (rank < k) {
                 A.out_ids[b * kst + rank] = (int32_t)(uint32_t)(v & 0xffffffffu);
                 A.out_dist[b * kst + rank] = __uint_as_float((uint32_t)(v >> 32));
             }
         }
-        if (real) atomicAdd(nreal, real);
+        real = __reduce_add_sync(0xffffffffu, real);  // one atomic per warp, not per key
+        if (lane == 0 && real) atomicAdd(nreal, real);
         __syncthreads();
         // fewer than k real keys, or a per-query k below the row length: pad the tail
         for (uint32_t t = min(*nreal, k) + threadIdx.x; t < kst; t += NT) {
@@ -1840,11 +1904,14 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     const uint64_t plane_bytes = 4ull * A.nstore * A.G;
     const uint64_t cent_bytes = 8ull * sk * ix->hmax;
     A.stage_cent = cent_bytes <= 65536 ? 1u : 0u;
-    const uint64_t s3_bytes = S3_BYTES + (A.stage_cent ? cent_bytes : 0);
+    const uint64_t s3_bytes = S3_BYTES + (A.stage_cent ? align16(cent_bytes) : 0);
     // S6 reuses the union: the distance histogram and survivors at its start,
     // the CTA's re-rank keys at its end
     const uint64_t keys_bytes = align16(8ull * A.sortP);
     const uint64_t s6_bytes = 4ull * NB + 8ull * SURV_CAP + keys_bytes;
+    // S3's copy of the cell offsets, where the region has room for it anyway
+    const uint64_t cells_bytes = 4ull * ((uint64_t)ix->K + 1);
+    if (s3_bytes + cells_bytes <= std::max(plane_bytes, s6_bytes)) A.o_cells = (uint32_t)s3_bytes;
     const uint64_t ubytes = align16(std::max(plane_bytes, std::max(s3_bytes, s6_bytes)));
     A.o_keys = (uint32_t)(o + ubytes - keys_bytes);
 
