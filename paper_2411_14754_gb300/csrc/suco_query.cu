@@ -318,53 +318,23 @@ __device__ __forceinline__ uint32_t next_pow2_dev(uint32_t x)
     return p;
 }
 
-// One warp sorts keys[0, cnt) (cnt <= 32*S) ascending in place: a bitonic
-// network over element e = slot*32 + lane held in registers; strides of 32 and
-// more pair slots of the same lane, smaller strides pair lanes (shuffles).
-template <int S>
-__device__ __forceinline__ void warp_sort_regs(unsigned long long (&v)[S])
+// Sorts in[0, n) ascending into out[0, n) by rank: the key at t goes to the
+// number of keys below it plus the number of equal keys before t.  Every
+// thread of a warp reads the same in[j] (a broadcast), the loads do not depend
+// on one another, and there is no chain of exchange steps as in a sorting
+// network; for the few keys it is used on (n <= 128) that is the shorter path.
+template <int NT>
+__device__ __forceinline__ void rank_sort(const unsigned long long* in, uint32_t n, unsigned long long* out)
 {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int size = 2; size <= 32 * S; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= 32) {
-                const int ds = stride >> 5;
-#pragma unroll
-                for (int lo = 0; lo < S; ++lo) {
-                    if (lo & ds) continue;
-                    const int hi = lo | ds;
-                    const bool asc = ((lo * 32 + lane) & size) == 0;
-                    const unsigned long long x = v[lo], y = v[hi];
-                    if ((x > y) == asc) {
-                        v[lo] = y;
-                        v[hi] = x;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int sl = 0; sl < S; ++sl) {
-                    const int e = sl * 32 + lane;
-                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[sl], stride);
-                    const bool lower = (e & stride) == 0, asc = (e & size) == 0;
-                    if (lower == asc ? o < v[sl] : o > v[sl]) v[sl] = o;
-                }
-            }
+    for (uint32_t t = threadIdx.x; t < n; t += NT) {
+        const unsigned long long v = in[t];
+        uint32_t rank = 0u;
+        for (uint32_t j = 0; j < n; ++j) {
+            const unsigned long long x = in[j];
+            rank += (uint32_t)(x < v) | ((uint32_t)(x == v) & (uint32_t)(j < t));
         }
+        out[rank] = v;
     }
-}
-
-template <int S>
-__device__ __forceinline__ void warp_sort_keys(unsigned long long* keys, uint32_t cnt)
-{
-    const int lane = threadIdx.x & 31;
-    unsigned long long v[S];
-#pragma unroll
-    for (int sl = 0; sl < S; ++sl) v[sl] = (uint32_t)(sl * 32 + lane) < cnt ? keys[sl * 32 + lane] : ~0ull;
-    warp_sort_regs<S>(v);
-#pragma unroll
-    for (int sl = 0; sl < S; ++sl) keys[sl * 32 + lane] = v[sl];
 }
 
 // Value bucket of a cell sum: monotone non-decreasing in s (FP32 subtract,
@@ -531,47 +501,29 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     unsigned long long prefix = 0, mask = 0, last_w = 0;
     int pass0 = 0;
     if (nm <= 32) {
-        // few members: one warp sorts them by key and walks the weight prefix
+        // few members: lane m adds up the weights of the members with smaller
+        // keys (broadcast loads, no dependent chain; keys are unique); the cut
+        // cell is the member whose weight interval covers the remaining need
         if (threadIdx.x < 32) {
-            unsigned long long key = lane < (int)nm ? mkey[lane] : ~0ull;
-            uint32_t w = lane < (int)nm ? mw[lane] : 0u;
-#pragma unroll
-            for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, stride);
-                    const uint32_t ow = __shfl_xor_sync(0xffffffffu, w, stride);
-                    const bool lower = (lane & stride) == 0;
-                    const bool asc = (lane & size) == 0;
-                    const bool take_other = lower == asc ? ok < key : ok > key;
-                    if (take_other) {
-                        key = ok;
-                        w = ow;
-                    }
-                }
-            }
-            uint32_t incl = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
+            const bool act = lane < (int)nm;
+            const unsigned long long key = act ? mkey[lane] : ~0ull;
+            const uint32_t w = act ? mw[lane] : 0u;
+            uint32_t excl = 0u;
+            for (uint32_t j = 0; j < nm; ++j) excl += mkey[j] < key ? mw[j] : 0u;
+            const uint32_t incl = excl + w;
             const uint32_t need = (uint32_t)(T - below);
-            const uint32_t hit = __ballot_sync(0xffffffffu, incl >= need && lane < (int)nm);
+            const uint32_t hit = __ballot_sync(0xffffffffu, act && excl < need && incl >= need);
             const int src = __ffs(hit) - 1;
-            const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
-            const uint32_t ii = __shfl_sync(0xffffffffu, incl, src);
-            if (lane == 0) {
-                bc[0] = kk;
-                bc[1] = ii;
+            if (lane == src) {
+                bc[0] = key;
+                bc[1] = incl;
             }
         }
-        __syncthreads();
+        __syncthreads();  // nothing writes bc again before the staircase's barrier
         prefix = bc[0];
         last_w = 0;
         below += bc[1];
         pass0 = 6;
-        __syncthreads();
     } else if (listed) {
         // bytes shared by every member are already decided
         unsigned long long* kmm = bc + 5;  // [5] = min, [6] = max
@@ -1535,8 +1487,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
                 uint32_t tot;
                 const uint32_t ex = block_exclusive_scan<NT>((isg << 16) | ise, wtmp, &tot);
                 const uint32_t gb4 = gcar + (ex >> 16), eb4 = ecar + (ex & 0xffffu);
-                if (isg || (ise && eb4 < need_eq)) {
-                    const uint32_t pos = gb4 + min(eb4, need_eq);
+                const uint32_t pos = gb4 + min(eb4, need_eq);
+                // pos < keep <= qC when the counts agree; the bound keeps a
+                // remote store inside the cluster's slots whatever they hold
+                if ((isg || (ise && eb4 < need_eq)) && pos < qC) {
                     const uint32_t owner = pos / qper, sl = pos - owner * qper;
                     st_cluster_u32(slot_base[owner] + 4u * sl, ids_in[t]);
                     const uint32_t sa = map_rank(smem_addr(sc_out + sl), owner);
@@ -1593,7 +1547,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
                     }
                     gm &= ~bit;
                     em &= ~bit;
-                    if (pos != 0xffffffffu) {
+                    if (pos < qC) {  // (0xffffffff: not taken; the bound keeps the store in the slots)
                         const uint32_t owner = pos / qper, sl = pos - owner * qper;
                         st_cluster_u32(slot_base[owner] + 4u * sl, base_id + (uint32_t)j);
                         if (multi) {
@@ -1667,7 +1621,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     uint32_t nbest = 0;
     if (nk <= 2 * k || nk <= 64) {
         if (nk <= 128) {
-            if (warp == 0) warp_sort_keys<4>(keys, nk);
+            rank_sort<NT>(keys, nk, surv);
+            best = surv;
             __syncthreads();
         } else {
             const uint32_t P = next_pow2_dev(nk);
@@ -1741,20 +1696,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
                 if (keep) surv[slot] = v;
             }
             __syncthreads();
-            if (ns <= 64) {
-                if (warp == 0) warp_sort_keys<2>(surv, ns);
+            if (ns <= 128) {
+                rank_sort<NT>(surv, ns, keys);  // the re-rank keys are no longer read
                 __syncthreads();
-            } else if (ns <= 128) {
-                if (warp == 0) warp_sort_keys<4>(surv, ns);
-                __syncthreads();
+                best = keys;
             } else {
                 uint32_t P = 1;
                 while (P < ns) P <<= 1;
                 for (uint32_t t = ns + threadIdx.x; t < P; t += NT) surv[t] = ~0ull;
                 __syncthreads();
                 block_bitonic_sort<NT>(surv, (int)P);
+                best = surv;
             }
-            best = surv;
             nbest = min(k, ns);
         } else {
             // a crowded bucket (many equal distances): sort the whole share
