@@ -110,6 +110,8 @@ struct QArgs {
     uint32_t sortP;       // power of two >= the CTA's candidate share (fallback sort)
     uint32_t stage_cent;  // 1: the subspace's centroids are staged in shared memory
     uint32_t o_cells;     // nonzero: the subspace's cell offsets are copied to o_union + o_cells for S3
+    uint32_t tab_copy;    // leading bytes of a subspace table that the other CTAs copy (a multiple of 16)
+    uint32_t o_qn;        // the next query's row, copied in while S6 runs
 };
 
 // ---------------------------------------------------------------------------
@@ -210,14 +212,16 @@ __device__ __forceinline__ Tab tab_at(char* smem, const QArgs& A, int i)
     char* t = smem + A.o_tab + (size_t)i * A.tab_stride;
     const int sk = A.sqrtK;
     Tab T;
+    // what the other CTAs read (the staircase and the rank -> centroid maps)
+    // comes first, in the tab_copy bytes they copy; the owner's S1-S3 state after
     T.kappa = reinterpret_cast<unsigned long long*>(t);
     T.teff = reinterpret_cast<unsigned long long*>(t + 8);
     T.row_pre = reinterpret_cast<uint32_t*>(t + 16);
-    T.d1 = reinterpret_cast<float*>(t + 20 + 4 * sk);
-    T.d2 = T.d1 + sk;
-    T.idx1 = reinterpret_cast<uint8_t*>(T.d2 + sk);
+    T.idx1 = reinterpret_cast<uint8_t*>(t + 20 + 4 * sk);
     T.idx2 = T.idx1 + sk;
-    T.r1 = T.idx2 + sk;
+    T.d1 = reinterpret_cast<float*>(t + A.tab_copy);
+    T.d2 = T.d1 + sk;
+    T.r1 = reinterpret_cast<uint8_t*>(T.d2 + sk);
     T.r2 = T.r1 + sk;
     return T;
 }
@@ -247,6 +251,38 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     }
     __syncthreads();
     const uint32_t res = wtmp[w] + incl - v;
+    *total = wtmp[32];
+    __syncthreads();
+    return res;
+}
+
+// The same over 64-bit values (two 32-bit sums carried in one scan).
+template <int NT>
+__device__ __forceinline__ unsigned long long block_exclusive_scan64(unsigned long long v, unsigned long long* wtmp,
+                                                                     unsigned long long* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtmp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned long long t = lane < NT / 32 ? wtmp[lane] : 0ull;
+        unsigned long long ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        wtmp[lane] = ti - t;
+        if (lane == 31) wtmp[32] = ti;
+    }
+    __syncthreads();
+    const unsigned long long res = wtmp[w] + incl - v;
     *total = wtmp[32];
     __syncthreads();
     return res;
@@ -690,7 +726,6 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
     // base | nibble flag}, and their flat starts
     uint4* seg_info = reinterpret_cast<uint4*>(smem + A.o_seg);          // [MAXSEG]
     uint32_t* seg_pre = reinterpret_cast<uint32_t*>(seg_info + MAXSEG);  // [MAXSEG+1]
-    uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
     const int sk = A.sqrtK;
     constexpr int EPT = (MAXSEG + NT - 1) / NT;
     uint32_t nqd[EPT], pP[EPT], pE[EPT], mode[EPT], s = 0, ne = 0;
@@ -728,9 +763,13 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
         s += nqd[u];
         ne += nqd[u] ? 1u : 0u;
     }
-    uint32_t F, M;
-    uint32_t run = block_exclusive_scan<NT>(s, wtmp, &F);
-    uint32_t slot = block_exclusive_scan<NT>(ne, wtmp, &M);
+    // quads (high half) and segments (low half, at most MAXSEG) in one scan;
+    // the radix histogram area of o_hist is free during S4
+    unsigned long long tot2;
+    const unsigned long long ex2 = block_exclusive_scan64<NT>(((unsigned long long)s << 32) | ne,
+                                                              reinterpret_cast<unsigned long long*>(smem + A.o_hist), &tot2);
+    const uint32_t F = (uint32_t)(tot2 >> 32), M = (uint32_t)tot2;
+    uint32_t run = (uint32_t)(ex2 >> 32), slot = (uint32_t)ex2;
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
         if (nqd[u]) {
@@ -791,15 +830,18 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
 #pragma unroll
             for (int u = 0; u < SCAN_U; ++u) {
                 const uint32_t idq[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+                // the segment's counter layout, once per quad: a nibble set
+                // puts id t of a group in word (t & 3), bits (t & 28)..+3; a
+                // one-bit plane puts it at bit t of one word
                 const bool nib = (md[u] >> 31) != 0u;
                 const uint32_t wbase = md[u] & 0x7fffffffu;
+                const uint32_t wstep = nib ? G : 0u, smask = nib ? 28u : 31u;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const uint32_t loc = idq[j] - id0;
                     if (((vmask[u] >> j) & 1u) && loc < span) {
                         const uint32_t t = loc & 31u;
-                        const uint32_t w = wbase + (nib ? (t & 3u) * G : 0u) + (loc >> 5);
-                        atomicAdd(&cnt_words[w], 1u << (nib ? (t & 28u) : t));
+                        atomicAdd(&cnt_words[wbase + (t & 3u) * wstep + (loc >> 5)], 1u << (t & smask));
                     }
                 }
             }
@@ -1214,6 +1256,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         sub_wb[i] = (uint32_t)i < ns15 ? (4u * ((uint32_t)i / 15u) * A.G) | 0x80000000u
                                        : (4u * A.nsets + (uint32_t)i - ns15) * A.G;
     }
+    bool q_next = false;  // the query row is already on its way to o_qn
     while (b < A.nq) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t grabbed = 0u;  // thread 0 of CTA 0: the query this cluster answers next
@@ -1248,8 +1291,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     }
     {
         float* qs = reinterpret_cast<float*>(smem + A.o_q);
-        const float* qg = A.Q + b * A.d;
-        for (int j = threadIdx.x; j < A.ldq; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
+        if (q_next) {
+            // copied in during the last query's S6 by this same thread (j
+            // strides match), so its own completed copies need no barrier
+            cp_async_wait_all();
+            const float* qn = reinterpret_cast<const float*>(smem + A.o_qn);
+            for (int j = threadIdx.x; j < A.ldq; j += NT) qs[j] = j < A.d ? qn[j] : 0.f;
+            q_next = false;
+        } else {
+            const float* qg = A.Q + b * A.d;
+            for (int j = threadIdx.x; j < A.ldq; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
+        }
         uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);
         for (int t = threadIdx.x; t < 2 * NC; t += NT) cnt[t] = 0u;
     }
@@ -1270,9 +1322,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     if (A.work && r == 0 && threadIdx.x == 0)
         for (int t = 0; t < CL; ++t) st_cluster_u32(map_rank(smem_addr(next_q), (uint32_t)t), grabbed);
 
-    // ---- copy the other CTAs' tables (16-byte loads: the stride is a multiple of 16)
+    // ---- copy the parts of the other CTAs' tables that S4 reads (16-byte
+    // loads: the table stride and the copied length are multiples of 16)
     {
-        const uint32_t vecs = A.tab_stride / 16;
+        const uint32_t vecs = A.tab_copy / 16;
         for (uint32_t t = threadIdx.x; t < (uint32_t)A.Ns * vecs; t += NT) {
             const int i = t / vecs;
             const uint32_t owner = (uint32_t)(i % CL);
@@ -1571,7 +1624,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         for (uint32_t t = threadIdx.x; t < mc; t += NT) A.dbg_cands[b * A.C + r * qper + t] = (int32_t)ids_out[t];
     }
 
-    // ---- S6: exact FP32 re-rank of this CTA's share of the candidates
+    // ---- S6: exact FP32 re-rank of this CTA's share of the candidates.  The
+    // next query is known since cluster barrier #2: its row is copied into
+    // o_qn meanwhile, for the next S0
+    {
+        const int64_t bn = A.work ? (int64_t)*reinterpret_cast<volatile uint32_t*>(next_q) : b + Gc;
+        if (bn < A.nq) {
+            const float* qg = A.Q + bn * A.d;
+            float* qn = reinterpret_cast<float*>(smem + A.o_qn);
+            for (int j = threadIdx.x; j < A.d; j += NT) cp_async4(qn + j, qg + j);
+            q_next = true;
+        }
+    }
     const uint32_t* slots = ids_out;
     const uint32_t mine = qC > r * qper ? min(qper, qC - r * qper) : 0u;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + A.o_keys);  // [sortP]
@@ -1815,7 +1879,8 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     const int NC = nsmax + 2;
     uint64_t o = 0;
     A.o_tab = (uint32_t)o;
-    A.tab_stride = align16(20 + 16ull * sk);
+    A.tab_copy = align16(20 + 6ull * sk);
+    A.tab_stride = align16(A.tab_copy + 10ull * sk);
     // the radix histograms of the survivor cut (S6) reuse the subspace tables'
     // region: no CTA reads a table after S4, and the next query's tables are
     // written only after cluster barrier #4, when every remote read of the
@@ -1824,6 +1889,8 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     o = align16(o + std::max<uint64_t>((uint64_t)ix->Ns * A.tab_stride, 4ull * 512));
     A.o_q = (uint32_t)o;
     A.ldq = (ix->d + 15) & ~15;
+    o = align16(o + 4ull * A.ldq);
+    A.o_qn = (uint32_t)o;
     o = align16(o + 4ull * A.ldq);
     A.o_hist = (uint32_t)o;
     o = align16(o + 4ull * (256 + 64));
