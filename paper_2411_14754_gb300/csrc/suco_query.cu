@@ -57,6 +57,7 @@ constexpr int MCAP = 1024;    // cells of the crossing bucket resolved from a li
 constexpr int SCAN_U = 4;     // 16-byte quads of ids in flight per lane in the scan
 
 constexpr int S3_BYTES = 4 * NB + 12 * MCAP;  // S3 scratch at the start of the union region
+constexpr int HIST_WORDS = 256 + 64;          // o_hist per S3 group: a 256-bin histogram, scan scratch
 constexpr int SURV_CAP = 512; // keys kept for the final sort of a local top-k
 constexpr int S6_CH = 4;      // float4 chunks per lane per row in one S6 load round
 
@@ -112,6 +113,8 @@ struct QArgs {
     uint32_t o_cells;     // nonzero: the subspace's cell offsets are copied to o_union + o_cells for S3
     uint32_t tab_copy;    // leading bytes of a subspace table that the other CTAs copy (a multiple of 16)
     uint32_t o_qn;        // the next query's row, copied in while S6 runs
+    uint32_t s3_stride;   // bytes of one S3 scratch group in the union region
+    uint32_t pair_ok;     // 1: a CTA that owns two subspaces ranks them at once, one per half
 };
 
 // ---------------------------------------------------------------------------
@@ -224,6 +227,46 @@ __device__ __forceinline__ Tab tab_at(char* smem, const QArgs& A, int i)
     T.r1 = reinterpret_cast<uint8_t*>(T.d2 + sk);
     T.r2 = T.r1 + sk;
     return T;
+}
+
+// Barrier over a group of NT threads (whole warps): id 0 with NT = the CTA's
+// size is __syncthreads(); ids 1 and 2 are the two halves of the CTA.
+template <int NT>
+__device__ __forceinline__ void group_sync(int bar)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory");
+}
+
+// Exclusive prefix sum over a group of NT threads (tid within the group,
+// barrier id bar); *total gets the group's sum.
+template <int NT>
+__device__ __forceinline__ uint32_t group_exclusive_scan(uint32_t v, uint32_t* wtmp, uint32_t* total, int tid, int bar)
+{
+    const int lane = tid & 31, w = tid >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtmp[w] = incl;
+    group_sync<NT>(bar);
+    if (w == 0) {
+        const uint32_t t = lane < NT / 32 ? wtmp[lane] : 0u;
+        uint32_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        wtmp[lane] = ti - t;
+        if (lane == 31) wtmp[32] = ti;
+    }
+    group_sync<NT>(bar);
+    const uint32_t res = wtmp[w] + incl - v;
+    *total = wtmp[32];
+    group_sync<NT>(bar);
+    return res;
 }
 
 template <int NT>
@@ -382,12 +425,16 @@ __device__ __forceinline__ int value_bucket(float s, float smin, float scale)
     return (int)t;
 }
 
-// S1-S3 for subspace i of query b (the CTA that owns i).
+// S1-S3 for subspace i of query b (the CTA that owns i), by a group of NT
+// threads: the whole CTA (tid = tid, barrier 0, scratch group 0), or
+// one half of it when the CTA ranks two subspaces at once (tid within the
+// half, named barrier 1 or 2, scratch group 0 or 1: its own S3 area of the
+// union, its own o_hist histograms and o_misc slots).
 template <int NT>
-__device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint32_t T)
+__device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint32_t T, int tid, int bar, int grp)
 {
     const int sk = A.sqrtK;
-    const int lane = threadIdx.x & 31;
+    const int lane = tid & 31;
     const float* qs = reinterpret_cast<const float*>(smem + A.o_q);
     Tab tb = tab_at(smem, A, i);
     const int soff = i * A.sub_s;
@@ -396,23 +443,23 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     // the subspace's cell offsets (the index's cell sizes) are copied to shared
     // memory while S1 and S2 run; S3 reads each of them up to twice
     const uint32_t* co = A.cell_off + (int64_t)i * (A.K + 1);
-    uint32_t* co_s = A.o_cells ? reinterpret_cast<uint32_t*>(smem + A.o_union + A.o_cells) : nullptr;
+    uint32_t* co_s = A.o_cells ? reinterpret_cast<uint32_t*>(smem + A.o_union + grp * A.s3_stride + A.o_cells) : nullptr;
     if (co_s)
-        for (int t = threadIdx.x; t <= A.K; t += NT) cp_async4(co_s + t, co + t);
+        for (int t = tid; t <= A.K; t += NT) cp_async4(co_s + t, co + t);
     // S1: squared distances to the 2*sqrtK half-subspace centroids.  The
     // subspace's centroids are staged dimension-major ([h][j][a]) so that
     // consecutive threads read consecutive words.
     const float* cg = A.cent + (int64_t)i * 2 * sk * A.hmax;
-    float* cst = reinterpret_cast<float*>(smem + A.o_union + S3_BYTES);
+    float* cst = reinterpret_cast<float*>(smem + A.o_union + grp * A.s3_stride + S3_BYTES);
     if (A.stage_cent) {
-        for (int t = threadIdx.x; t < 2 * sk * A.hmax; t += NT) {
+        for (int t = tid; t < 2 * sk * A.hmax; t += NT) {
             const int j = t % A.hmax, ha = t / A.hmax;
             const int h = ha >= sk, a = ha - h * sk;
             cst[(h * A.hmax + j) * sk + a] = __ldg(cg + t);
         }
-        __syncthreads();
+        group_sync<NT>(bar);
     }
-    for (int t = threadIdx.x; t < 2 * sk; t += NT) {
+    for (int t = tid; t < 2 * sk; t += NT) {
         const int h = t >= sk;
         const int a = t - h * sk;
         if (A.dtab_in) {  // tables of the tensor-core ranking
@@ -437,9 +484,9 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
         }
         (h ? tb.d2 : tb.d1)[a] = acc;
     }
-    __syncthreads();
+    group_sync<NT>(bar);
     // S2: stable ranks and their inverses
-    for (int t = threadIdx.x; t < 2 * sk; t += NT) {
+    for (int t = tid; t < 2 * sk; t += NT) {
         const int h = t >= sk;
         const int a = t - h * sk;
         const float* dd = h ? tb.d2 : tb.d1;
@@ -452,16 +499,16 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
         (h ? tb.r2 : tb.r1)[a] = (uint8_t)r;
         (h ? tb.idx2 : tb.idx1)[r] = (uint8_t)a;
     }
-    __syncthreads();
+    group_sync<NT>(bar);
 
     // S3: the cut key kappa*
-    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + A.o_union);                // [NB]
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + A.o_union + grp * A.s3_stride);  // [NB]
     unsigned long long* mkey = reinterpret_cast<unsigned long long*>(hist + NB);    // [MCAP]
     uint32_t* mw = reinterpret_cast<uint32_t*>(mkey + MCAP);                        // [MCAP]
-    uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + 256;
-    uint32_t* h256 = reinterpret_cast<uint32_t*>(smem + A.o_hist);
-    unsigned long long* bc = reinterpret_cast<unsigned long long*>(smem + A.o_misc);
-    uint32_t* mcount = reinterpret_cast<uint32_t*>(smem + A.o_misc) + 14;
+    uint32_t* wtmp = reinterpret_cast<uint32_t*>(smem + A.o_hist) + grp * HIST_WORDS + 256;
+    uint32_t* h256 = reinterpret_cast<uint32_t*>(smem + A.o_hist) + grp * HIST_WORDS;
+    unsigned long long* bc = reinterpret_cast<unsigned long long*>(smem + A.o_misc + 64 * grp);  // [7] per group
+    uint32_t* mcount = reinterpret_cast<uint32_t*>(smem + A.o_misc + 64 * grp) + 14;
     auto cell_size = [&](uint32_t x) -> uint32_t {
         return co_s ? co_s[x + 1] - co_s[x] : __ldg(co + x + 1) - __ldg(co + x);
     };
@@ -472,14 +519,14 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     // 2-D mapping of threads onto cells: 2^lg threads per centroid row
     int lg = 0;
     while ((1 << lg) < sk) ++lg;
-    const int c_of = threadIdx.x & ((1 << lg) - 1);
-    const int a_of = threadIdx.x >> lg;
+    const int c_of = tid & ((1 << lg) - 1);
+    const int a_of = tid >> lg;
     const int a_step = NT >> lg;
 
-    for (int t = threadIdx.x; t < NB; t += NT) hist[t] = 0u;
-    if (threadIdx.x == 0) *mcount = 0u;
+    for (int t = tid; t < NB; t += NT) hist[t] = 0u;
+    if (tid == 0) *mcount = 0u;
     if (co_s) cp_async_wait_all();
-    __syncthreads();
+    group_sync<NT>(bar);
     if (c_of < sk) {
         const float d2c = tb.d2[c_of];
         for (int a = a_of; a < sk; a += a_step) {
@@ -488,22 +535,22 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
             if (w) atomicAdd(&hist[value_bucket(__fadd_rn(tb.d1[a], d2c), smin, scale)], w);
         }
     }
-    __syncthreads();
+    group_sync<NT>(bar);
     // crossing bucket: exclusive prefix < T <= inclusive prefix
     {
         constexpr int BPT = NB / NT > 0 ? NB / NT : 1;
         uint32_t v[BPT], s = 0;
 #pragma unroll
         for (int u = 0; u < BPT; ++u) {
-            const int e = threadIdx.x * BPT + u;
+            const int e = tid * BPT + u;
             v[u] = e < NB ? hist[e] : 0u;
             s += v[u];
         }
         uint32_t tot;
-        uint32_t run = block_exclusive_scan<NT>(s, wtmp, &tot);
+        uint32_t run = group_exclusive_scan<NT>(s, wtmp, &tot, tid, bar);
 #pragma unroll
         for (int u = 0; u < BPT; ++u) {
-            const int e = threadIdx.x * BPT + u;
+            const int e = tid * BPT + u;
             if (e < NB && run < T && run + v[u] >= T) {
                 bc[3] = (unsigned long long)e;
                 bc[4] = run;
@@ -511,7 +558,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
             run += v[u];
         }
     }
-    __syncthreads();
+    group_sync<NT>(bar);
     const int bstar = (int)bc[3];
     unsigned long long below = bc[4];
     // members of the crossing bucket (non-empty cells only)
@@ -531,7 +578,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
             }
         }
     }
-    __syncthreads();
+    group_sync<NT>(bar);
     const uint32_t nm = *mcount;
     const bool listed = nm <= MCAP;
     unsigned long long prefix = 0, mask = 0, last_w = 0;
@@ -540,7 +587,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
         // few members: lane m adds up the weights of the members with smaller
         // keys (broadcast loads, no dependent chain; keys are unique); the cut
         // cell is the member whose weight interval covers the remaining need
-        if (threadIdx.x < 32) {
+        if (tid < 32) {
             const bool act = lane < (int)nm;
             const unsigned long long key = act ? mkey[lane] : ~0ull;
             const uint32_t w = act ? mw[lane] : 0u;
@@ -555,7 +602,7 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
                 bc[1] = incl;
             }
         }
-        __syncthreads();  // nothing writes bc again before the staircase's barrier
+        group_sync<NT>(bar);  // nothing writes bc again before the staircase's barrier
         prefix = bc[0];
         last_w = 0;
         below += bc[1];
@@ -563,34 +610,34 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     } else if (listed) {
         // bytes shared by every member are already decided
         unsigned long long* kmm = bc + 5;  // [5] = min, [6] = max
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             kmm[0] = ~0ull;
             kmm[1] = 0ull;
         }
-        __syncthreads();
+        group_sync<NT>(bar);
         unsigned long long lo = ~0ull, hi = 0ull;
-        for (uint32_t m = threadIdx.x; m < nm; m += NT) {
+        for (uint32_t m = tid; m < nm; m += NT) {
             lo = min(lo, mkey[m]);
             hi = max(hi, mkey[m]);
         }
         if (lo != ~0ull) atomicMin(&kmm[0], lo);
         if (hi) atomicMax(&kmm[1], hi);
-        __syncthreads();
+        group_sync<NT>(bar);
         const unsigned long long diff = kmm[0] ^ kmm[1];
         while (pass0 < 6 && ((diff >> (40 - 8 * pass0)) & 255ull) == 0) {
             mask |= 255ull << (40 - 8 * pass0);
             ++pass0;
         }
         prefix = kmm[0] & mask;
-        __syncthreads();
+        group_sync<NT>(bar);
     }
     // weighted radix select of the cut key over the bucket's members
     for (int pass = pass0; pass < 6; ++pass) {
         const int shift = 40 - 8 * pass;
-        for (int t = threadIdx.x; t < 256; t += NT) h256[t] = 0u;
-        __syncthreads();
+        for (int t = tid; t < 256; t += NT) h256[t] = 0u;
+        group_sync<NT>(bar);
         if (listed) {
-            for (uint32_t m = threadIdx.x; m < nm; m += NT) {
+            for (uint32_t m = tid; m < nm; m += NT) {
                 const unsigned long long key = mkey[m];
                 if ((key & mask) == prefix) atomicAdd(&h256[(key >> shift) & 255u], mw[m]);
             }
@@ -608,8 +655,8 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
                 if (w) atomicAdd(&h256[(key >> shift) & 255u], w);
             }
         }
-        __syncthreads();
-        if (threadIdx.x < 32) {
+        group_sync<NT>(bar);
+        if (tid < 32) {
             uint32_t v[8];
             uint32_t s = 0;
 #pragma unroll
@@ -643,17 +690,17 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
                 bc[2] = wbin;
             }
         }
-        __syncthreads();
+        group_sync<NT>(bar);
         prefix |= bc[0] << shift;
         mask |= 255ull << shift;
         below += bc[1];
         last_w = bc[2];
-        __syncthreads();
+        group_sync<NT>(bar);
     }
     // after the warp path `below` already counts the cut cell itself
     // the staircase: retrieved cells of ranked row rho are its first columns in
     // r2 order (the key grows along the row); store lengths, then prefix sums
-    for (int rho = threadIdx.x; rho < sk; rho += NT) {
+    for (int rho = tid; rho < sk; rho += NT) {
         const int a = tb.idx1[rho];
         const float d1a = tb.d1[a];
         int lo = 0, hi = sk;  // number of columns with key <= kappa*
@@ -664,8 +711,8 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
         }
         tb.row_pre[rho + 1] = (uint32_t)lo;
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
+    group_sync<NT>(bar);
+    if (tid < 32) {
         constexpr int RPL = 8;  // sqrtK <= 256 rows, 8 per lane
         uint32_t v[RPL], s = 0;
 #pragma unroll
@@ -694,17 +741,17 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
             *tb.teff = below + last_w;
         }
     }
-    __syncthreads();
-    if (A.dbg_teff && threadIdx.x == 0) A.dbg_teff[b * A.Ns + i] = (int64_t)*tb.teff;
+    group_sync<NT>(bar);
+    if (A.dbg_teff && tid == 0) A.dbg_teff[b * A.Ns + i] = (int64_t)*tb.teff;
     if (A.dbg_dtab)
-        for (int t = threadIdx.x; t < 2 * sk; t += NT)
+        for (int t = tid; t < 2 * sk; t += NT)
             A.dbg_dtab[(b * A.Ns + i) * 2 * sk + t] = t < sk ? tb.d1[t] : tb.d2[t - sk];
     if (A.dbg_act)
-        for (int x = threadIdx.x; x < A.K; x += NT) {
+        for (int x = tid; x < A.K; x += NT) {
             const int a = x / sk, c = x - a * sk;
             A.dbg_act[(b * A.Ns + i) * A.K + x] = cell_key(tb.d1[a], tb.d2[c], tb.r1[a], tb.r2[c]) <= prefix;
         }
-    __syncthreads();
+    group_sync<NT>(bar);
 }
 
 // S4 for entries [e0, e0+m) of the flattened retrieved-cell list (all
@@ -1309,7 +1356,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
 
     const uint32_t qT = qpar[0], qC = qpar[1], qk = qpar[2], qper = qpar[3];
     // ---- S1-S3 for the subspaces this CTA owns
-    for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT>(A, smem, b, i, qT);
+    if (A.pair_ok && (int)r + CL < A.Ns && (int)r + 2 * CL >= A.Ns) {
+        // two subspaces: each half of the CTA ranks one (named barriers 1, 2)
+        const int grp = threadIdx.x >= NT / 2;
+        rank_subspace<NT / 2>(A, smem, b, (int)r + grp * CL, qT, (int)threadIdx.x - grp * (NT / 2), 1 + grp, grp);
+        __syncthreads();  // both halves are done with their scratch before the union is cleared
+    } else {
+        for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT>(A, smem, b, i, qT, (int)threadIdx.x, 0, 0);
+    }
     // clear the bit planes (the union region served as S3 scratch)
     {
         uint4* pw = reinterpret_cast<uint4*>(smem + A.o_union);
@@ -1893,7 +1947,7 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     A.o_qn = (uint32_t)o;
     o = align16(o + 4ull * A.ldq);
     A.o_hist = (uint32_t)o;
-    o = align16(o + 4ull * (256 + 64));
+    o = align16(o + 4ull * 2 * HIST_WORDS);  // two S3 groups
     A.o_misc = (uint32_t)o;
     o = align16(o + 4ull * 160);
 
@@ -1933,6 +1987,10 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     const uint64_t cells_bytes = 4ull * ((uint64_t)ix->K + 1);
     if (s3_bytes + cells_bytes <= std::max(plane_bytes, s6_bytes)) A.o_cells = (uint32_t)s3_bytes;
     const uint64_t ubytes = align16(std::max(plane_bytes, std::max(s3_bytes, s6_bytes)));
+    // two S3 groups side by side fit in the union, and each half of the CTA
+    // has a thread for every centroid column (the 2-D cell mapping of S3)
+    A.s3_stride = align16(s3_bytes + (A.o_cells ? cells_bytes : 0));
+    A.pair_ok = (2ull * A.s3_stride <= ubytes && (uint32_t)(NT / 2) >= next_pow2((uint32_t)sk)) ? 1u : 0u;
     A.o_keys = (uint32_t)(o + ubytes - keys_bytes);
 
     o = align16(o + ubytes);
