@@ -4,7 +4,8 @@
 // cluster loops over its share of the batch.
 //
 // Stages inside the kernel (one launch, no global scratch):
-//   S0  the query row is staged in shared memory.
+//   S0  the query row is staged in shared memory (copied in during the
+//       previous query's S6 when the next query is already known).
 //   S1  squared half-subspace centroid distances d1[a], d2[c] in FP32
 //       (acc = fma(q_j - c_j, q_j - c_j, acc) over j ascending).
 //   S2  stable ranks r1[a], r2[c] of those distances (ties by centroid index)
@@ -14,20 +15,21 @@
 //       collected, so the retrieved cells are exactly those with key <= kappa*,
 //       where kappa* is the smallest key whose cumulative cell size reaches T.
 //       kappa* is found by a weighted histogram over linear value buckets of
-//       the cell sums (one pass over the K cells), then a weighted radix select
-//       over the few cells of the bucket that crosses T.  Because the key grows
-//       along every ranked row, the retrieved cells of a row form a prefix of
-//       that row in r2 order: the retrieved set is a "staircase", published as
-//       row prefix sums.  CTA r handles the subspaces i with i % CL == r.
+//       the cell sums (one pass over the K cells), then among the few cells of
+//       the bucket that crosses T (by counting smaller keys, or a weighted radix
+//       select when the bucket is crowded).  Because the key grows along every
+//       ranked row, the retrieved cells of a row form a prefix of that row in
+//       r2 order: the retrieved set is a "staircase", published as row prefix
+//       sums.  CTA r handles the subspaces i with i % CL == r (two at once, one
+//       per half of the CTA, when it owns two).
 //   S4  SC-score counting (Definition 4).  Each CTA owns a contiguous id range
-//       and keeps its SC-scores bit-sliced in shared memory: B = bits(Ns) planes
-//       of one bit per id.  It lists its part of every retrieved cell's id list
-//       of every subspace (the index's chunk splits), load-balances the
-//       flattened list over warps and adds 1 to each listed id's count with a
-//       ripple of shared-memory atomicXor: level j is toggled, and the carry
-//       moves to level j+1 while the returned old bit was 1.  For m toggles of a
-//       bit that starts at 0, exactly floor(m/2) return 1 whatever their order,
-//       so concurrent increments of the same id still count exactly.
+//       and keeps the ids' SC-score counters in shared memory (4-bit counters
+//       for up to 15 subspaces, one-bit planes past them).  It lists its part
+//       of every retrieved cell's id list of every subspace (the index's chunk
+//       splits), load-balances the flattened list over warps in 16-byte quads
+//       of ids and adds 1 to each listed id's counter with one shared-memory
+//       atomicAdd (an id occurs at most once per subspace, so a counter never
+//       overflows); the counters are then turned into B = bits(Ns) bit planes.
 //   S5  candidate selection.  Per-warp counts of scores >= s (bitwise
 //       comparisons of the sliced counts) are summed over the cluster through
 //       distributed shared memory; theta is the largest s with at least C
@@ -35,7 +37,7 @@
 //       (C in total) are written, in id order, straight into the candidate
 //       slots of the CTA that re-ranks them.
 //   S6  exact re-rank: every CTA computes FP32 squared distances of its share
-//       of the C candidates (one warp per row, several rows in flight per warp),
+//       of the C candidates (8 lanes per row, several rows in flight per warp),
 //       keeps a local top-k by (distance, id), and CTA 0 merges the CL sorted
 //       lists by rank.
 #include <algorithm>
@@ -54,12 +56,14 @@ namespace {
 constexpr int MAXSEG = 512;   // retrieved-cell segments listed per scan round
 constexpr int NB = 1024;      // linear value buckets of the cut search
 constexpr int MCAP = 1024;    // cells of the crossing bucket resolved from a list
-constexpr int SCAN_U = 4;     // 16-byte quads of ids in flight per lane in the scan
+constexpr int SCAN_U = 3;     // 16-byte quads of ids in flight per lane in the scan
 
 constexpr int S3_BYTES = 4 * NB + 12 * MCAP;  // S3 scratch at the start of the union region
 constexpr int HIST_WORDS = 256 + 64;          // o_hist per S3 group: a 256-bin histogram, scan scratch
 constexpr int SURV_CAP = 512; // keys kept for the final sort of a local top-k
-constexpr int S6_CH = 4;      // float4 chunks per lane per row in one S6 load round
+// 16-byte chunks per lane per row in one S6 load round: 4 for rows of fewer
+// than 64 chunks (one round covers a 512-byte row), 2 for longer rows (measured)
+constexpr int S6_CH_SHORT = 4, S6_CH_LONG = 2;
 
 struct QArgs {
     const float* __restrict__ X;
@@ -976,7 +980,7 @@ __device__ __forceinline__ uint32_t bitsliced_ge(const uint32_t acc[B], uint32_t
 // into keys (distance bits << 32 | id; ~0 for an id outside [0, n)).  8 lanes
 // per row, two groups of 4 rows per warp in flight; each lane keeps S6_CH
 // float4 chunks of each of its two rows in registers per load round.
-template <int NT>
+template <int NT, int S6_CH>
 __device__ void rerank_fp32(const QArgs& A, const float4* q4, const uint32_t* ids, uint32_t count,
                             unsigned long long* keys)
 {
@@ -1070,7 +1074,7 @@ __device__ __forceinline__ float bf16x8_sqdiff(uint4 w, const float4* q, float a
 
 // S6 coarse pass: squared distances of the BF16 copies of the rows listed in
 // ids[0, count), accumulated in FP32, into keys (same layout as rerank_fp32).
-template <int NT>
+template <int NT, int S6_CH>
 __device__ void rerank_bf16(const QArgs& A, const float4* q4, const uint32_t* ids, uint32_t count,
                             unsigned long long* keys)
 {
@@ -1696,13 +1700,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
     uint32_t nk = mine;  // keys of this CTA that enter the local top-k
     if (A.precision == 0 || qC <= A.R) {
-        rerank_fp32<NT>(A, q4, slots, mine, keys);
+        if (A.ld / 4 >= 64)
+            rerank_fp32<NT, S6_CH_LONG>(A, q4, slots, mine, keys);
+        else
+            rerank_fp32<NT, S6_CH_SHORT>(A, q4, slots, mine, keys);
         __syncthreads();
     } else {
         // coarse pass on the reduced-precision copy, then the R smallest
         // coarse keys of the whole cluster survive into the exact pass
         if (A.precision == 1)
-            rerank_bf16<NT>(A, q4, slots, mine, keys);
+            if (A.ldh / 8 >= 64)
+                rerank_bf16<NT, S6_CH_LONG>(A, q4, slots, mine, keys);
+            else
+                rerank_bf16<NT, S6_CH_SHORT>(A, q4, slots, mine, keys);
         else
             rerank_fp8<NT>(A, q4, slots, mine, keys);
         __syncthreads();
@@ -1724,7 +1734,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         }
         __syncthreads();
         nk = *ns;
-        rerank_fp32<NT>(A, q4, surv_ids, nk, keys);
+        if (A.ld / 4 >= 64)
+            rerank_fp32<NT, S6_CH_LONG>(A, q4, surv_ids, nk, keys);
+        else
+            rerank_fp32<NT, S6_CH_SHORT>(A, q4, surv_ids, nk, keys);
         __syncthreads();
     }
 
