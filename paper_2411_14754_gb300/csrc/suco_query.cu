@@ -61,8 +61,8 @@ constexpr int SCAN_U = 3;     // 16-byte quads of ids in flight per lane in the 
 constexpr int S3_BYTES = 4 * NB + 12 * MCAP;  // S3 scratch at the start of the union region
 constexpr int HIST_WORDS = 256 + 64;          // o_hist per S3 group: a 256-bin histogram, scan scratch
 constexpr int SURV_CAP = 512; // keys kept for the final sort of a local top-k
-// 16-byte chunks per lane per row in one S6 load round: 4 for rows of fewer
-// than 64 chunks (one round covers a 512-byte row), 2 for longer rows (measured)
+// 16-byte chunks per lane per row in one S6 load round: 2 for rows of 64 to
+// 127 chunks, 4 otherwise (measured at 32, 64 and 240 chunks)
 constexpr int S6_CH_SHORT = 4, S6_CH_LONG = 2;
 
 struct QArgs {
@@ -1687,7 +1687,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     // o_qn meanwhile, for the next S0
     {
         const int64_t bn = A.work ? (int64_t)*reinterpret_cast<volatile uint32_t*>(next_q) : b + Gc;
-        if (bn < A.nq) {
+        if (A.o_qn && bn < A.nq) {
             const float* qg = A.Q + bn * A.d;
             float* qn = reinterpret_cast<float*>(smem + A.o_qn);
             for (int j = threadIdx.x; j < A.d; j += NT) cp_async4(qn + j, qg + j);
@@ -1700,7 +1700,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
     uint32_t nk = mine;  // keys of this CTA that enter the local top-k
     if (A.precision == 0 || qC <= A.R) {
-        if (A.ld / 4 >= 64)
+        if (A.ld / 4 >= 64 && A.ld / 4 < 128)
             rerank_fp32<NT, S6_CH_LONG>(A, q4, slots, mine, keys);
         else
             rerank_fp32<NT, S6_CH_SHORT>(A, q4, slots, mine, keys);
@@ -1709,7 +1709,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         // coarse pass on the reduced-precision copy, then the R smallest
         // coarse keys of the whole cluster survive into the exact pass
         if (A.precision == 1)
-            if (A.ldh / 8 >= 64)
+            if (A.ldh / 8 >= 64 && A.ldh / 8 < 128)
                 rerank_bf16<NT, S6_CH_LONG>(A, q4, slots, mine, keys);
             else
                 rerank_bf16<NT, S6_CH_SHORT>(A, q4, slots, mine, keys);
@@ -1734,7 +1734,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         }
         __syncthreads();
         nk = *ns;
-        if (A.ld / 4 >= 64)
+        if (A.ld / 4 >= 64 && A.ld / 4 < 128)
             rerank_fp32<NT, S6_CH_LONG>(A, q4, surv_ids, nk, keys);
         else
             rerank_fp32<NT, S6_CH_SHORT>(A, q4, surv_ids, nk, keys);
@@ -1929,7 +1929,11 @@ struct Layout {
     size_t smem = 0;
 };
 
-int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uint32_t C, int k, Layout* L)
+// One shared-memory layout.  pair: room for two S3 scratch groups (a CTA
+// that owns two subspaces ranks them at once when they fit); qn: a buffer for
+// the next query's row.
+int layout_once(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uint32_t C, int k, bool pair, bool qn,
+                Layout* L)
 {
     QArgs& A = L->A;
     memset(&A, 0, sizeof(A));
@@ -1957,10 +1961,12 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     A.o_q = (uint32_t)o;
     A.ldq = (ix->d + 15) & ~15;
     o = align16(o + 4ull * A.ldq);
-    A.o_qn = (uint32_t)o;
-    o = align16(o + 4ull * A.ldq);
+    if (qn) {
+        A.o_qn = (uint32_t)o;
+        o = align16(o + 4ull * A.ldq);
+    }
     A.o_hist = (uint32_t)o;
-    o = align16(o + 4ull * 2 * HIST_WORDS);  // two S3 groups
+    o = align16(o + 4ull * (pair ? 2 : 1) * HIST_WORDS);  // one per S3 group
     A.o_misc = (uint32_t)o;
     o = align16(o + 4ull * 160);
 
@@ -2003,11 +2009,29 @@ int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     // two S3 groups side by side fit in the union, and each half of the CTA
     // has a thread for every centroid column (the 2-D cell mapping of S3)
     A.s3_stride = align16(s3_bytes + (A.o_cells ? cells_bytes : 0));
-    A.pair_ok = (2ull * A.s3_stride <= ubytes && (uint32_t)(NT / 2) >= next_pow2((uint32_t)sk)) ? 1u : 0u;
+    A.pair_ok = (pair && 2ull * A.s3_stride <= ubytes && (uint32_t)(NT / 2) >= next_pow2((uint32_t)sk)) ? 1u : 0u;
     A.o_keys = (uint32_t)(o + ubytes - keys_bytes);
 
     o = align16(o + ubytes);
     L->smem = o;
+    return SUCO_OK;
+}
+
+// The layout of a launch shape: the paired S3 scratch and the next-row buffer
+// are added only where they cost no CTAs per SM (228 KB of shared memory per
+// SM, 1 KB reserved per CTA; 64 registers a thread allow 1024 / NT CTAs).
+int make_layout(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uint32_t C, int k, Layout* L)
+{
+    auto ctas = [&](const Layout& l) {
+        return std::min<uint64_t>(233472ull / (l.smem + 1024ull), (uint64_t)(1024 / NT));
+    };
+    Layout best, t;
+    layout_once(ix, CL, npass, nsmax, NT, C, k, false, false, &best);
+    layout_once(ix, CL, npass, nsmax, NT, C, k, true, false, &t);
+    if (t.A.pair_ok && ctas(t) >= ctas(best)) best = t;
+    layout_once(ix, CL, npass, nsmax, NT, C, k, best.A.pair_ok != 0, true, &t);
+    if (ctas(t) >= ctas(best)) best = t;
+    *L = best;
     return SUCO_OK;
 }
 
