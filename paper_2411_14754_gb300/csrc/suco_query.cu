@@ -1982,7 +1982,7 @@ int layout_once(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     A.run_stride = (A.per_cta + 15) & ~15u;
     A.o_run = (uint32_t)o;
     if (npass > 1) o = align16(o + 10ull * A.run_stride);
-    // at least 128: the warp sort of a small share writes 128 keys back
+    // at least 128: the rank sort of up to 128 top-k survivors writes them here
     A.sortP = next_pow2(std::max<uint32_t>(A.per_cta, 128));
     A.o_union = (uint32_t)o;
     A.nbits = nsmax == 8 ? 4 : (nsmax == 16 ? 5 : 6);
