@@ -308,10 +308,12 @@ SUCO_API int suco_thresholds(int64_t n, double alpha, double beta, int32_t k, in
  * device global memory, defined in the library and held by every GPU that
  * loads it until the process exits.  All calls share that array: calls whose
  * GPU work overlaps in time (other streams, other host threads) race on it.
- * The first call on a device looks up the array's device address once; make
- * that first call before any stream capture.  The call synchronises `stream`
- * once (it reads back the data's largest magnitude to choose the fixed-point
- * scale of the sums). */
+ * The first call on a device looks up the array's device address once.
+ * Every call synchronises `stream` once (it reads the data's largest
+ * magnitude back to the host to choose the fixed-point scale of the sums), so
+ * no call can be captured into a CUDA graph.  The call raises, and never
+ * lowers, the dynamic shared-memory limits of the K-means kernels it shares
+ * with suco_build_index. */
 SUCO_API int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int32_t dim_off, int32_t dim_len,
                                  int32_t k, int32_t iters, float* centroids, int32_t* assign, void* stream);
 

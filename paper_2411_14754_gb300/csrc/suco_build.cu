@@ -211,6 +211,18 @@ __global__ void split_kernel(const uint32_t* __restrict__ cell_off, const int32_
     }
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` and never
+// lowers it: the K-means kernels are shared by the index build and the
+// allocation-free entry point, which may run from different host threads.
+template <class K>
+cudaError_t raise_smem_limit(K* kern, size_t bytes)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess || (size_t)fa.maxDynamicSharedSizeBytes >= bytes) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 int grid_for(int64_t work, int threads, int cap = 65535)
 {
     int64_t g = (work + threads - 1) / threads;
@@ -303,11 +315,8 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
     if (assign_smem > (size_t)dev_smem_optin)
         return fail(SUCO_EUNSUPPORTED, "centroid table of %zu bytes exceeds shared memory", assign_smem);
     const int use_smem = accum_smem <= (size_t)dev_smem_optin ? 1 : 0;
-    SUCO_CUDA_TRY(cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)assign_smem));
-    if (use_smem)
-        SUCO_CUDA_TRY(cudaFuncSetAttribute(kmeans_accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)accum_smem));
+    SUCO_CUDA_TRY(raise_smem_limit(kmeans_assign_kernel, assign_smem));
+    if (use_smem) SUCO_CUDA_TRY(raise_smem_limit(kmeans_accum_kernel, accum_smem));
     int nsm = 0;
     SUCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ix->device));
     const dim3 g_assign(grid_for(n, 256, 8 * nsm), H);
@@ -436,17 +445,8 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
     const size_t accum_smem = (size_t)k * dim_len * 8 + (size_t)k * 4;
     const int use_smem = accum_smem <= (size_t)smem_optin ? 1 : 0;
     // raise (never lower) the dynamic shared-memory limits of the shared kernels
-    cudaFuncAttributes fa;
-    SUCO_CUDA_TRY(cudaFuncGetAttributes(&fa, kmeans_assign_kernel));
-    if ((size_t)fa.maxDynamicSharedSizeBytes < assign_smem)
-        SUCO_CUDA_TRY(cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)assign_smem));
-    if (use_smem) {
-        SUCO_CUDA_TRY(cudaFuncGetAttributes(&fa, kmeans_accum_kernel));
-        if ((size_t)fa.maxDynamicSharedSizeBytes < accum_smem)
-            SUCO_CUDA_TRY(cudaFuncSetAttribute(kmeans_accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)accum_smem));
-    }
+    SUCO_CUDA_TRY(raise_smem_limit(kmeans_assign_kernel, assign_smem));
+    if (use_smem) SUCO_CUDA_TRY(raise_smem_limit(kmeans_accum_kernel, accum_smem));
     const dim3 g_assign(grid_for(n, 256, 8 * nsm), 1);
     const dim3 g_accum(grid_for(n, 256, 2 * nsm), 1);
     for (int it = 0; it < iters; ++it) {

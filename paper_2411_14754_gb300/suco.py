@@ -111,6 +111,24 @@ def _stream(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def _same_device(x, ref, name):
+    if x.device != ref.device:
+        raise ValueError(f"{name} is on {x.device}, the data on {ref.device}")
+
+
+def _check_assign_out(assign, n, device):
+    """An int32 output of n entries that a kernel writes: anything shorter,
+    wider, strided or on another device would be written out of bounds."""
+    if not isinstance(assign, torch.Tensor) or assign.dtype != torch.int32:
+        raise TypeError("assign must be an int32 tensor")
+    if not assign.is_contiguous():
+        raise ValueError("assign must be contiguous")
+    if assign.numel() < n:
+        raise ValueError(f"assign holds {assign.numel()} entries, {n} are written")
+    if assign.device != device:
+        raise ValueError(f"assign is on {assign.device}, the data on {device}")
+
+
 def _dev_f32(x, name):
     if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
         raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
@@ -335,10 +353,13 @@ def suco_kmeans_noalloc(data: torch.Tensor, dim_off: int, dim_len: int, centroid
     _dev_f32(centroids, "centroids")
     n, d = data.shape
     k = centroids.shape[0]
-    if centroids.shape[1] != dim_len:
+    if centroids.dim() != 2 or centroids.shape[1] != dim_len:
         raise ValueError("centroids must be k x dim_len")
+    _same_device(centroids, data, "centroids")
     if assign is None:
         assign = torch.empty(n, dtype=torch.int32, device=data.device)
+    else:
+        _check_assign_out(assign, n, data.device)
     _check(load_library().suco_kmeans_noalloc(_ptr(data), n, d, dim_off, dim_len, k, iters, _ptr(centroids),
                                               _ptr(assign), _stream(stream)))
     return assign

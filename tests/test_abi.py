@@ -76,3 +76,28 @@ def test_host_side_argument_errors(lib):
     lib.suco_free.argtypes = [ctypes.c_void_p]
     lib.suco_free(None)  # NULL-safe
     assert lib.suco_version() == 100
+
+
+def test_noalloc_assign_output_is_checked_before_any_launch():
+    # the K-means kernel writes n int32 values into assign: a tensor that is
+    # short, of another type, strided or on another device is refused on the host
+    torch = pytest.importorskip("torch")
+    from paper_2411_14754_gb300 import suco as S
+    cpu = torch.device("cpu")
+    S._check_assign_out(torch.empty(10, dtype=torch.int32), 10, cpu)
+    S._check_assign_out(torch.empty(12, dtype=torch.int32), 10, cpu)
+    with pytest.raises(TypeError):
+        S._check_assign_out(torch.empty(10, dtype=torch.int16), 10, cpu)
+    with pytest.raises(TypeError):
+        S._check_assign_out(torch.empty(10, dtype=torch.int64), 10, cpu)
+    with pytest.raises(TypeError):
+        S._check_assign_out(None, 10, cpu)
+    with pytest.raises(ValueError):
+        S._check_assign_out(torch.empty(9, dtype=torch.int32), 10, cpu)
+    with pytest.raises(ValueError):
+        S._check_assign_out(torch.empty(20, dtype=torch.int32)[::2], 10, cpu)
+    with pytest.raises(ValueError):
+        S._check_assign_out(torch.empty(10, dtype=torch.int32, device="meta"), 10, cpu)
+    with pytest.raises(ValueError):
+        S._same_device(torch.empty(3, device="meta"), torch.empty(3), "centroids")
+    S._same_device(torch.empty(3), torch.empty(3), "centroids")

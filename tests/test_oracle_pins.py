@@ -391,3 +391,51 @@ def test_batch_driver_matches_single_queries():
         o = oracle.query(X, idx, Q[b], 7, T=75, C_=30, debug=False)
         assert ids[b].tolist() == o["ids"].tolist()
         np.testing.assert_array_equal(dist[b], o["dist"])
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 4 from given half-subspace distance tables (Algorithm 4 computes
+# the tables, then ranks cells from them; the tensor-core ranking's parity
+# goes through this entry)
+
+_STAGES = ("teff", "activated", "scores", "cands", "ids", "dist")
+
+
+def test_query_from_tables_given_the_queries_own_tables_equals_the_query():
+    X = W.random_data(31, 2500, 24, kind="gauss")
+    idx = _small_index(X, 3, 6, iters=3, seed=32)
+    for qq in W.random_data(33, 6, 24, kind="gauss"):
+        o = oracle.query(X, idx, qq, 9, T=200, C_=40, rank_precision=1)
+        t = oracle.query_from_tables(X, idx, qq, 9, T=200, C_=40, dtab=o["dtab"])
+        for key in _STAGES:
+            np.testing.assert_array_equal(t[key], o[key], err_msg=key)
+
+
+def test_query_from_tables_written_from_the_definition_equals_the_fp64_query():
+    # integer rows and integer centroids (no Lloyd update): every half-subspace
+    # squared distance is an integer below 2^24, exact in FP32 and FP64.  The
+    # tables are written here from the definition (per half, sum of squared
+    # differences over the half's dims); ranking from them must reproduce the
+    # FP64 query in every stage, and the FP64 query's own tables must equal them.
+    n, d, Ns, sk = 2000, 22, 3, 5          # d not a multiple of Ns: the last subspace is longer
+    X = W.random_data(34, n, d, kind="int")
+    idx = _small_index(X, Ns, sk, iters=0, seed=35)
+    cent = idx["centroids"].astype(np.float64)
+    for qq in W.random_data(36, 5, d, kind="int"):
+        tab = np.empty((Ns, 2, sk))
+        for i in range(Ns):
+            s = d // Ns
+            off = i * s
+            ln = d - (Ns - 1) * s if i == Ns - 1 else s
+            halves = ((off, ln // 2), (off + ln // 2, ln - ln // 2))
+            for h, (ho, hl) in enumerate(halves):
+                diff = cent[i, h, :, :hl] - qq[ho:ho + hl].astype(np.float64)[None, :]
+                tab[i, h] = (diff * diff).sum(axis=1)
+        o = oracle.query(X, idx, qq, 8, T=120, C_=35, rank_precision=0)
+        np.testing.assert_array_equal(o["dtab"], tab)
+        t = oracle.query_from_tables(X, idx, qq, 8, T=120, C_=35, dtab=tab)
+        for key in _STAGES:
+            np.testing.assert_array_equal(t[key], o[key], err_msg=key)
+        # a transposed table (halves swapped) must change the ranking somewhere
+        sw = oracle.query_from_tables(X, idx, qq, 8, T=120, C_=35, dtab=tab[:, ::-1, :].copy())
+        assert not np.array_equal(sw["activated"], o["activated"])

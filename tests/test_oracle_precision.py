@@ -92,3 +92,41 @@ def test_e4m3_rows_use_one_scale_per_subspace():
     big = np.abs(X) > 2.0 ** -6 * np.repeat(s, 4)[None, :]
     rel = np.abs(Xh - X)[big] / np.abs(X)[big]
     assert rel.max() <= 2.0 ** -4 + 1e-12
+
+
+def test_bf16_centroid_tables_on_bf16_exact_data_are_the_fp64_distances():
+    # integers in [0, 16) and centroids that are data rows (no Lloyd update)
+    # are exact in BF16: the tables are then the FP64 squared distances of the
+    # raw half-vectors, and the norms |q_h|^2 + |c|^2 by direct sums
+    from scipy.spatial.distance import cdist
+    from paper_2411_14754_gb300 import workloads as W
+    n, d, Ns, sk = 1500, 20, 2, 7
+    X = W.random_data(41, n, d, kind="int")
+    idx = oracle.build_index(X, Ns, sk, 0, W.random_init_ids(42, n, Ns, sk))
+    for q in W.random_data(43, 4, d, kind="int"):
+        tab, norms = P.bf16_centroid_tables(idx, q)
+        for i in range(Ns):
+            for h in range(2):
+                off, ln = oracle.half_dims(d, Ns, i, h)
+                c = idx["centroids"][i, h, :, :ln].astype(np.float64)
+                qh = q[off:off + ln].astype(np.float64)
+                np.testing.assert_array_equal(tab[i, h], cdist(qh[None, :], c, "sqeuclidean")[0])
+                np.testing.assert_array_equal(norms[i, h], np.dot(qh, qh) + np.einsum("ij,ij->i", c, c))
+
+
+def test_bf16_centroid_tables_round_both_operands_like_torch():
+    # on general data the tables are the distances of the BF16-rounded vectors
+    # (rounding by torch's bfloat16 cast, a library conversion)
+    from paper_2411_14754_gb300 import workloads as W
+    n, d, Ns, sk = 1200, 24, 3, 6
+    X = W.random_data(44, n, d, kind="gauss") * 7.3
+    idx = oracle.build_index(X, Ns, sk, 2, W.random_init_ids(45, n, Ns, sk))
+    q = W.random_data(46, 1, d, kind="gauss")[0] * 7.3
+    tab, _ = P.bf16_centroid_tables(idx, q)
+    qb = torch.from_numpy(q).to(torch.bfloat16).double().numpy()
+    for i in range(Ns):
+        for h in range(2):
+            off, ln = oracle.half_dims(d, Ns, i, h)
+            cb = torch.from_numpy(np.ascontiguousarray(idx["centroids"][i, h, :, :ln])).to(torch.bfloat16).double()
+            ref = ((cb.numpy() - qb[off:off + ln][None, :]) ** 2).sum(axis=1)
+            np.testing.assert_allclose(tab[i, h], ref, rtol=1e-14, atol=0)
