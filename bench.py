@@ -59,11 +59,13 @@ def parse():
                    "beta even where the workload trains the ratio network")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
     p.add_argument("--exact-rerank", type=int, default=512, help="survivors of the BF16/FP8 coarse re-rank")
+    p.add_argument("--guard", type=float, default=0.002,
+                   help="operating points are chosen on the validation split at target + guard")
     p.add_argument("--margin-candidates", type=int, default=6,
                    help="cheapest margin pairs (by modelled bytes) timed for the learned arm")
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
                    help="re-rank precision of the fixed-ratio path")
-    p.add_argument("--rank-precision", default="fp32", choices=["fp32", "bf16"],
+    p.add_argument("--rank-precision", default="fp32", choices=["fp32", "bf16", "fp8"],
                    help="centroid-distance arithmetic of the fixed-ratio path (bf16: tensor cores)")
     return p.parse_args()
 
@@ -72,10 +74,11 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
-def workload_config(w, batch):
-    return {"workload": f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, alpha={w.alpha}, "
-                        f"beta={w.beta}, k={w.k}, FP32",
-            "stands_in_for": w.stands_in_for, "queries": w.nq, "batch": batch,
+def workload_config(w, batch=None):
+    """The workload as both arms name it (the method each arm runs is reported
+    outside this dict)."""
+    return {"workload": f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, k={w.k}",
+            "stands_in_for": w.stands_in_for, "queries": w.nq, "batch": w.batch if batch is None else batch,
             "l2": "inputs larger than L2 (dataset copy in HBM >> 129 MB)", "parallelism": "query-sharded replicas"}
 
 
@@ -188,7 +191,62 @@ def run_cpu_baseline(w, X, Q, threads, alpha=None, beta=None, target_s=15.0):
             "seconds": dt}
 
 
+def run_cpu_baseline_on_index(pkg, index, w, X, Q, gt, T, C, target_s=10.0):
+    """The FP64 oracle (Algorithms 3-4) answering from the GPU's own index
+    (exported with suco_export_index) at the same per-query thresholds T_b and
+    C_b, single-threaded and with OpenMP over queries on every host core.  Each
+    run is a bounded sample (about target_s seconds of CPU work, sized by a
+    probe); its recall@k is measured against the same exact k-NN."""
+    import oracle
+    from paper_2411_14754_gb300 import learn as L
+    ex = pkg.suco_export_index(index)
+    idx = dict(Ns=w.Ns, sqrtK=w.sqrtK, centroids=ex["centroids"], cell_off=ex["cell_off"].astype(np.int64),
+               perm=ex["perm"].astype(np.int64))
+    T = np.asarray(T, dtype=np.int64)
+    C = np.asarray(C, dtype=np.int64)
+    runs = {}
+    for threads in sorted({1, oracle.max_threads()}):
+        probe = min(len(Q), 2 * threads)
+        t0 = time.time()
+        oracle.query_batch(X, idx, Q[:probe], w.k, T[:probe], C[:probe], rank_precision=0, nthreads=threads)
+        per_q = (time.time() - t0) / probe
+        m = int(min(len(Q), max(probe, round(target_s / max(per_q, 1e-9)))))
+        t0 = time.time()
+        ids, _ = oracle.query_batch(X, idx, Q[:m], w.k, T[:m], C[:m], rank_precision=0, nthreads=threads)
+        dt = time.time() - t0
+        runs[threads] = {"value": m / dt, "queries": m, "seconds": dt,
+                         "recall_at_k": float(L.recall_rows(ids, gt[:m]).mean())}
+    allc = max(runs)
+    return {"value": runs[allc]["value"], "unit": UNIT, "cores": allc, "kind": "oracle",
+            "sample": (f"the first {runs[allc]['queries']} evaluation queries, FP64 oracle (Algorithms 3-4) on the "
+                       f"GPU-built index (suco_export_index) at the same per-query T_b, C_b, OpenMP over queries on "
+                       f"{allc} host threads"),
+            "seconds": runs[allc]["seconds"], "recall_at_k": runs[allc]["recall_at_k"],
+            "single_thread": runs[1], "index": "the GPU-built index, exported", "mean_T": float(T[:runs[allc]['queries']].mean()),
+            "mean_C": float(C[:runs[allc]["queries"]].mean())}
+
+
+def exact_knn_host(X, Qs, k, shortlist=64, chunk=64):
+    """Exact k nearest ids (ties by id) on the host: an FP32 matrix product
+    shortlists candidates, FP64 differences decide among them."""
+    xn = (X.astype(np.float64) ** 2).sum(1)
+    out = np.empty((len(Qs), k), np.int64)
+    for s0 in range(0, len(Qs), chunk):
+        q = Qs[s0:s0 + chunk]
+        d = xn[None, :] - 2.0 * (q @ X.T).astype(np.float64)
+        cand = np.argpartition(d, shortlist, axis=1)[:, :shortlist]
+        for j in range(len(q)):
+            c = cand[j]
+            ex = ((X[c].astype(np.float64) - q[j].astype(np.float64)) ** 2).sum(1)
+            out[s0 + j] = c[np.lexsort((c, ex))[:k]]
+    return out
+
+
 def run_reference(args):
+    """The oracle (FP64, Algorithms 3-4, OpenMP over queries) on the host cores:
+    the workload's own index build (same initial ids, same Lloyd iterations,
+    untimed) and its fixed ratios alpha, beta; each step answers a bounded
+    sample of the evaluation queries."""
     rank, _, world = dist_env()
     if rank != 0:
         return
@@ -197,29 +255,79 @@ def run_reference(args):
     w = W.WORKLOADS[args.workload]
     X = W.dataset(w.number)
     Q = W.queries(w.number)
-    threads = os.cpu_count() or 1
+    threads = oracle.max_threads()
     T = oracle.collision_threshold(w.alpha, w.n)
     C = oracle.candidate_count(w.beta, w.n, w.k)
-    idx = oracle.build_index(X, w.Ns, w.sqrtK, 2, W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK), nthreads=threads)
+    idx = oracle.build_index(X, w.Ns, w.sqrtK, w.kmeans_iters, W.kmeans_init_ids(w.number, w.n, w.Ns, w.sqrtK),
+                             nthreads=threads)
     per_step = max(threads, 16)
     times = []
+    answered = []
     for s in range(args.warmup + args.steps):
-        qs = Q[(s * per_step) % (w.nq - per_step):][:per_step]
+        q0 = (s * per_step) % (w.nq - per_step)
+        qs = Q[q0:q0 + per_step]
         t0 = time.time()
-        oracle.query_batch(X, idx, qs, w.k, T, C, rank_precision=0, nthreads=threads)
+        ids, _ = oracle.query_batch(X, idx, qs, w.k, T, C, rank_precision=0, nthreads=threads)
         if s >= args.warmup:
             times.append(time.time() - t0)
+            answered.append((q0, ids))
     tot = sum(times)
     value = per_step * len(times) / tot
+    qsel = np.concatenate([np.arange(q0, q0 + per_step) for q0, _ in answered])
+    gt = exact_knn_host(X, Q[qsel], w.k)
+    got = np.concatenate([ids for _, ids in answered])
+    rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w.k for a, b in zip(got, gt)]))
     sample = (f"{per_step} queries per step of the same workload through the FP64 CPU oracle "
-              f"(Algorithms 3-4), OpenMP over queries on {threads} host threads")
+              f"(Algorithms 3-4) at alpha={w.alpha}, beta={w.beta}, OpenMP over queries on {threads} host threads")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, per_step), "impl": "reference",
+            "config": workload_config(w), "impl": "reference",
+            "method": {"arm": "CPU oracle", "alpha": w.alpha, "beta": w.beta, "index_lloyd_iterations": w.kmeans_iters},
+            "recall_at_k": rec,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def precision_report(pkg, index, w, X, q0, ids_s, dist_s, rec, args, gt):
+    """Relative error |d - d64| / d64 of every returned squared distance (max,
+    p99), recall against FP32 and, for a tensor-core ranking, the relative
+    error of its half-subspace tables against the FP64 squared distances of the
+    unrounded query and centroids."""
+    ids = ids_s.cpu().numpy()
+    dist = dist_s.cpu().numpy().astype(np.float64)
+    Q = q0.cpu().numpy()
+    rel = []
+    for j in range(len(Q)):
+        ok = ids[j] >= 0
+        d64 = ((X[ids[j][ok]].astype(np.float64) - Q[j].astype(np.float64)[None, :]) ** 2).sum(1)
+        rel.append(np.abs(dist[j][ok] - d64) / np.maximum(d64, 1e-300))
+    rel = np.concatenate(rel)
+    out = {"result_rel_error_max": float(rel.max()), "result_rel_error_p99": float(np.percentile(rel, 99)),
+           "queries": int(len(Q))}
+    if args.precision != "fp32" or args.rank_precision != "fp32":
+        from oracle import recall as _recall
+        ids32, _ = pkg.suco_query_batch(index, q0, w.k, w.alpha, w.beta)
+        out["recall_fp32"] = _recall(ids32.cpu().numpy(), np.stack(gt))
+        out["recall_delta_vs_fp32"] = rec - out["recall_fp32"]
+    if args.rank_precision != "fp32":
+        dbg = pkg.suco_query_debug(index, q0, w.k, w.alpha, w.beta, want=("dtab",), precision=args.precision,
+                                   rank_precision=args.rank_precision, exact_rerank=args.exact_rerank)
+        tab = dbg["dtab"].cpu().numpy().astype(np.float64)
+        cent = pkg.suco_export_index(index)["centroids"].astype(np.float64)
+        s = w.d // w.Ns
+        terr = []
+        for i in range(w.Ns):
+            ln = w.d - (w.Ns - 1) * s if i == w.Ns - 1 else s
+            for h, (ho, hl) in enumerate(((i * s, ln // 2), (i * s + ln // 2, ln - ln // 2))):
+                qh = Q[:, ho:ho + hl].astype(np.float64)
+                ref = ((qh[:, None, :] - cent[i, h, None, :, :hl]) ** 2).sum(-1)
+                terr.append((np.abs(tab[:, i, h, :] - ref) / np.maximum(ref, 1e-300)).ravel())
+        terr = np.concatenate(terr)
+        out["rank_table_rel_error_median"] = float(np.median(terr))
+        out["rank_table_rel_error_p99"] = float(np.percentile(terr, 99))
+    return out
 
 
 # fixed (alpha, beta) points the plain arm may take; its operating point is the
@@ -305,17 +413,31 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
                              precision=cur["precision"], exact_rerank=args.exact_rerank)
         return qb.shape[0]
 
-    # learned operating point per re-rank precision: the smallest margin that
-    # reaches the target; the faster of the two precisions is the learned arm
-    # margins added to the network's log alpha and log beta: every pair of a
-    # grid is tried, the pairs reaching the target are ranked by modelled
-    # bytes, and the cheapest few are timed in both re-rank precisions
+    # Operating points are chosen on the validation split of the training
+    # queries only (held out from the network's training, never the evaluation
+    # queries), at the target plus a guard band of about two standard errors
+    # of that split's mean recall; the evaluation recall is then measured and
+    # reported as it comes out.
+    Qv, gv = model.validation["Q"], model.validation["gt"]
+    sel_target = target + args.guard
+    vb = [Qv[i:i + B] for i in range(0, Qv.shape[0], B)]
+
+    def val_recall_learned(prec):
+        al, be = L.predict(index, model, Qv)
+        ids, _ = pkg.suco_query_batch(index, Qv, w.k, L.FALLBACK[0], L.BETA_RANGE[1], alpha_per_query=al,
+                                      beta_per_query=be, precision=prec, exact_rerank=args.exact_rerank)
+        return float(L.recall_rows(ids.cpu().numpy(), gv).mean())
+
+    # learned arm: margins added to the network's log alpha and log beta; every
+    # pair of a grid is tried on the validation split, the pairs reaching the
+    # selection target are ranked by modelled bytes, and the cheapest few are
+    # timed in both re-rank precisions; the fastest is the learned arm
     by_prec = {}
     for prec in ("fp32", "bf16"):
-        cands = L.margin_grid(index, model, Qe, gt, w.k, target=target, precision=prec,
+        cands = L.margin_grid(index, model, Qv, gv, w.k, target=sel_target, precision=prec,
                               exact_rerank=args.exact_rerank)[:args.margin_candidates]
         if not cands:  # nothing reaches the target: the common margin search's answer
-            m, r = L.tune_offsets(index, model, Qe, gt, w.k, target=target, precision=prec,
+            m, r = L.tune_offsets(index, model, Qv, gv, w.k, target=sel_target, precision=prec,
                                   exact_rerank=args.exact_rerank)
             cands = [(0.0, m, m, r)]
         best = None
@@ -325,15 +447,16 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
             ms, _ = time_loop(torch, stream, 2 * nb, 2, learned_step)
             qps = 2 * w.nq / (ms / 1000.0)
             if best is None or qps > best["qps_probe"]:
-                best = {"margin": [ma, mb], "recall_at_k": r, "qps_probe": qps, "modelled_bytes": cost}
+                best = {"margin": [ma, mb], "val_recall": r, "qps_probe": qps, "modelled_bytes": cost}
         by_prec[prec] = best
-        note(f"learned {prec}: margins {best['margin']}, recall {best['recall_at_k']:.4f}, "
+        note(f"learned {prec}: margins {best['margin']}, validation recall {best['val_recall']:.4f}, "
              f"probe {best['qps_probe']:.0f} q/s")
-    ok = [p for p in by_prec if by_prec[p]["recall_at_k"] >= target] or list(by_prec)
-    learned_prec = max(ok, key=lambda p: by_prec[p]["qps_probe"])
-    margin, rec_learned = by_prec[learned_prec]["margin"], by_prec[learned_prec]["recall_at_k"]
+    learned_prec = max(by_prec, key=lambda p: by_prec[p]["qps_probe"])
+    margin = by_prec[learned_prec]["margin"]
     model.offsets = tuple(margin)
     cur.update(st=model.struct(), precision=learned_prec)
+    ids_e, _ = L.query_learned(index, model, Qe, w.k, precision=learned_prec, exact_rerank=args.exact_rerank)
+    rec_learned = float(L.recall_rows(ids_e.cpu().numpy(), gt).mean())
     st = cur["st"]
 
     def plain_step_fn(alpha, beta):
@@ -343,19 +466,22 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
                                  stream=stream)
         return f
 
-    # plain operating point: fastest grid point whose recall reaches the target
+    # plain arm: the fastest grid point whose validation recall reaches the selection target
     plain = None
     rec_grid = {}
     for a in PLAIN_ALPHAS:
         for bt in PLAIN_BETAS:
-            ids, _ = pkg.suco_query_batch(index, Qe, w.k, a, bt)
-            r = float(L.recall_rows(ids.cpu().numpy(), gt).mean())
+            ids, _ = pkg.suco_query_batch(index, Qv, w.k, a, bt)
+            r = float(L.recall_rows(ids.cpu().numpy(), gv).mean())
             rec_grid[f"{a},{bt}"] = r
-            if r >= target:
+            if r >= sel_target:
                 ms, _ = time_loop(torch, stream, 2 * nb, 2, plain_step_fn(a, bt))
                 qps = 2 * w.nq / (ms / 1000.0)
                 if plain is None or qps > plain["qps_probe"]:
-                    plain = {"alpha": a, "beta": bt, "recall_at_k": r, "qps_probe": qps}
+                    plain = {"alpha": a, "beta": bt, "val_recall": r, "qps_probe": qps}
+    if plain is not None:
+        ids, _ = pkg.suco_query_batch(index, Qe, w.k, plain["alpha"], plain["beta"])
+        plain["recall_at_k"] = float(L.recall_rows(ids.cpu().numpy(), gt).mean())
     note(f"plain operating point: {plain}")
     setup_s = time.time() - t_setup
 
@@ -438,20 +564,25 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as _o
-        pa, pb = (plain["alpha"], plain["beta"]) if plain else (w.alpha, w.beta)
-        cpu = run_cpu_baseline(w, X, Qall, _o.max_threads(), alpha=pa, beta=pb, target_s=args.cpu_seconds)
+        al, be = L.predict(index, model, Qe)
+        a_np, b_np = al.cpu().numpy(), be.cpu().numpy()
+        Tq = [_o.collision_threshold(float(a), w.n) for a in a_np]
+        Cq = [_o.candidate_count(min(float(b), L.BETA_RANGE[1]), w.n, w.k) for b in b_np]
+        cpu = run_cpu_baseline_on_index(pkg, index, w, X, Qall, gt, Tq, Cq, target_s=args.cpu_seconds / 2)
+        cpu["operating_point"] = "the learned arm's per-query alpha_b, beta_b (thresholds T_b, C_b)"
 
     if rank == 0:
-        cfg = workload_config(w, B)
-        cfg["workload"] = (f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, k={w.k}, learned per-query "
-                           f"alpha/beta (MLP {3 * w.Ns}-{model.H}-2, GELU, BF16 weights), "
-                           + ("FP32 re-rank" if learned_prec == "fp32" else
-                              f"BF16 coarse re-rank + exact FP32 re-rank of the top {R}"))
-        cfg["n_train"] = n_train
+        cfg = workload_config(w)
+        method = {"arm": "learned per-query alpha/beta", "network": f"MLP {3 * w.Ns}-{model.H}-2, GELU, BF16 weights",
+                  "n_train": n_train, "rerank": ("FP32" if learned_prec == "fp32" else
+                                                 f"{learned_prec.upper()} coarse + exact FP32 top {R}"),
+                  "selection": (f"margins and precision chosen on the {Qv.shape[0]} validation queries of the training "
+                                f"set at recall >= {sel_target:.3f}; recall_at_k measured on the {w.nq} evaluation "
+                                f"queries")}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": cfg, "recall_at_k": rec_learned, "k": w.k, "target_recall": target,
+                "config": cfg, "method": method, "recall_at_k": rec_learned, "k": w.k, "target_recall": target,
                 "margin": margin, "learned_precision": learned_prec, "learned_by_precision": by_prec,
                 "plain_fp32": plain_line,
                 "speedup_vs_plain": (value / plain_line["value"]) if plain_line else None,
@@ -461,7 +592,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
                         "d2h_bytes_per_step": d2h // args.steps},
                 "clocks": clk.summary(), "gpu_launches": 2 * args.steps,
                 "index_build_s": build_s, "train_s": train_s, "setup_s": setup_s,
-                "training": rep, "plain_grid_recall": rec_grid}
+                "training": rep, "plain_grid_val_recall": rec_grid}
         print(json.dumps(line), flush=True)
     pkg.suco_free(index)
 
@@ -589,12 +720,13 @@ def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
                                target_s=args.cpu_seconds)
     if rank == 0:
         cfg = workload_config(w, B)
-        cfg["workload"] = (f"{w.name}: n={w.n}, d={w.d}, Ns={w.Ns}, sqrtK={w.sqrtK}, beta={w.beta}, per-query k in "
-                           f"{list(w.k_mix)} and alpha in {list(w.alpha_mix)} drawn uniformly, FP32")
+        method = {"arm": (f"beta={w.beta}, per-query k in {list(w.k_mix)} and alpha in {list(w.alpha_mix)} drawn "
+                          f"uniformly, FP32")}
         cfg["launch"] = {"cluster_size": shape[0], "threads": shape[1], "cuda_graphs": True, "persistent": True}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": mean_launch_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+                "method": method,
                 "recall_at_k": rec, "recall_note": "mean over a sample of recall@k_b with each query's own k_b",
                 "t_eff_per_query": teff, "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
@@ -739,6 +871,11 @@ def main():
     del Xg
     rec = _recall(ids_s.cpu().numpy(), np.stack(gt))
     teff_total = float(dbg["t_eff"].double().sum(dim=1).mean().item())
+    # per-result error of the returned squared distances against FP64, and, for
+    # a reduced-precision mode, its recall change against FP32 on the same
+    # queries and the error of its cell-ranking tables against the FP64
+    # distances of the unrounded vectors
+    err = precision_report(pkg, index, w, X, q0, ids_s, dist_s, rec, args, gt)
     T, Cc = pkg.suco_thresholds(w.n, w.alpha, w.beta, w.k)
 
     peaks = measured_peaks()
@@ -766,18 +903,17 @@ def main():
 
     if rank == 0:
         cfg = workload_config(w, B)
-        if args.precision != "fp32" or args.rank_precision != "fp32":
-            cfg["workload"] += (f", re-rank {args.precision} (exact FP32 on the top {args.exact_rerank}), "
-                                f"cell ranking {args.rank_precision}")
+        method = {"arm": f"fixed alpha={w.alpha}, beta={w.beta}", "rerank": args.precision,
+                  "exact_rerank": args.exact_rerank, "cell_ranking": args.rank_precision}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": cfg, "recall_at_k": rec, "k": w.k,
-                "T": T, "C": Cc, "t_eff_per_query": teff_total,
+                "config": cfg, "method": method, "recall_at_k": rec, "k": w.k,
+                "T": T, "C": Cc, "t_eff_per_query": teff_total, "precision_report": err,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                         "d2h_bytes_per_step": d2h // args.steps},
-                "clocks": clk.summary(), "gpu_launches": args.steps * (2 if args.rank_precision == "bf16" else 1),
+                "clocks": clk.summary(), "gpu_launches": args.steps * (2 if args.rank_precision != "fp32" else 1),
                 "index_build_s": build_s}
         print(json.dumps(line), flush=True)
     pkg.suco_free(index)

@@ -139,6 +139,13 @@ SUCO_API int suco_build_index_from_assignments(const float* data, int64_t n, int
  * the GPU (they share the workspace). */
 #define SUCO_RANK_FP32 0
 #define SUCO_RANK_BF16 1
+/* FP8 (not in the paper): the same tensor-core computation with E4M3 operands
+ * (tcgen05 kind::f8f6f4) and one scale per subspace: the centroids are coded
+ * with the dataset's scale s_i of the FP8 copy, each query with its own
+ * t_bi = (largest |q| over subspace i) / 448; the codes' products are summed on
+ * the tensor cores, and the sum is multiplied by s_i * t_bi in FP32.  Needs
+ * the workspace (SUCO_COPY_RANK_BF16) and the FP8 copy (SUCO_COPY_FP8). */
+#define SUCO_RANK_FP8 2
 
 typedef struct suco_query_params {
     int32_t k;            /* results per query (the maximum if k_per_query), 1..256   */
@@ -167,7 +174,8 @@ typedef struct suco_query_params {
  * Asynchronous on `stream`; allocates nothing.  nq = 0 is a no-op.
  * Errors: SUCO_EINVAL (NULL pointer, k/alpha/beta out of range),
  * SUCO_EUNSUPPORTED (the per-query SC-score array of n bytes, split over the
- * cluster, or the candidate share does not fit in shared memory), SUCO_ECUDA. */
+ * cluster, or the candidate share does not fit in shared memory), SUCO_ECUDA,
+ * SUCO_ETIMEOUT (the index's status word is set: see suco_read_status). */
 SUCO_API int suco_query_batch(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
                      int32_t* out_ids, float* out_dist, void* stream);
 
@@ -194,8 +202,8 @@ SUCO_API int suco_query_debug(const suco_index* index, const float* queries, int
  * device memory; synchronous.  Errors: SUCO_EINVAL (NULL index, unknown bits),
  * SUCO_ENOMEM, SUCO_ECUDA. */
 #define SUCO_COPY_BF16 1
-/* mask bit 1 (SUCO_COPY_RANK_BF16): reserve the workspace of the BF16
- * tensor-core ranking, 4096 x Ns x 2 x sqrtK FP32 values. */
+/* mask bit 1 (SUCO_COPY_RANK_BF16): reserve the workspace of the tensor-core
+ * ranking (BF16 and FP8), 4096 x Ns x 2 x sqrtK FP32 values. */
 #define SUCO_COPY_RANK_BF16 2
 /* mask bit 2 (SUCO_COPY_FP8): the FP8 E4M3 copy (n x ceil16(d) bytes, zero
  * padded) and its per-subspace scales; it serves SUCO_PRECISION_FP8. */
@@ -317,13 +325,38 @@ SUCO_API int suco_thresholds(int64_t n, double alpha, double beta, int32_t k, in
 SUCO_API int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int32_t dim_off, int32_t dim_len,
                                  int32_t k, int32_t iters, float* centroids, int32_t* assign, void* stream);
 
-/* Reads and clears the index's device status word.  Kernels never spin
- * without a limit: a wait on the tensor-core ranking's MMA completion gives up
- * after about one second, sets SUCO_STATUS_WAIT_TIMEOUT here, and the launch
- * ends with unreliable tables instead of hanging.  0 means every launch since
+/* Reads and clears the index's status word.  Kernels never spin without a
+ * limit: a wait on the tensor-core ranking's MMA completion gives up after
+ * about one second, stores SUCO_STATUS_WAIT_TIMEOUT in the word (which lives
+ * in mapped host memory), and the launch ends with unreliable tables instead
+ * of hanging.  While the word is set, suco_query_batch and suco_query_debug on
+ * that index return SUCO_ETIMEOUT without launching (a wait that gives up
+ * inside a call's own launch is seen by the next call, or by the same call
+ * when the word was set before its query launch).  0 means every launch since
  * the last read completed normally.  Synchronises the device. */
 #define SUCO_STATUS_WAIT_TIMEOUT 1u
 SUCO_API int suco_read_status(suco_index* index, uint32_t* status);
+
+/* Failure injection for tests (no counterpart in the paper).  Arms one fault,
+ * process-wide, that fires at the `after`-th event of its kind from now (0 =
+ * the next one) and then disarms itself:
+ *   SUCO_FAULT_ALLOC         an allocation (device memory, the pinned status
+ *                            word, or the host index object) fails as an
+ *                            out-of-memory would: the call returns SUCO_ENOMEM
+ *                            and releases what it had allocated;
+ *   SUCO_FAULT_LAUNCH        a kernel launch reports failure (the query kernel
+ *                            is then not launched): SUCO_ECUDA;
+ *   SUCO_FAULT_WAIT_TIMEOUT  the tensor-core ranking launch behaves as if its
+ *                            bounded wait had given up: it writes no tables and
+ *                            sets the index's status word, which the query
+ *                            entry point reports as SUCO_ETIMEOUT.
+ * SUCO_FAULT_NONE disarms.  Nothing here faults, traps or stalls a GPU.
+ * Errors: SUCO_EINVAL for an unknown kind or after < 0. */
+#define SUCO_FAULT_NONE 0
+#define SUCO_FAULT_ALLOC 1
+#define SUCO_FAULT_LAUNCH 2
+#define SUCO_FAULT_WAIT_TIMEOUT 3
+SUCO_API int suco_inject_fault(int32_t kind, int32_t after);
 
 /* Releases the index and its device memory.  NULL-safe. */
 SUCO_API void suco_free(suco_index* index);

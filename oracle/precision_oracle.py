@@ -56,26 +56,17 @@ def e4m3_values():
 
 def quantize_e4m3(x):
     """float -> E4M3 codes (uint8): nearest finite value, ties to the even
-    code (mantissa LSB 0), magnitudes beyond 448 saturated."""
-    vals = e4m3_values()
-    finite = np.where(~np.isnan(vals))[0]
-    fv = vals[finite]
+    code (mantissa LSB 0), magnitudes beyond 448 saturated, the sign bit of a
+    negative input kept.  The non-negative codes 0x00..0x7E have increasing
+    values, so the magnitude's two neighbours are found by a sorted search."""
+    pos = e4m3_values()[:0x7F]
     x = np.clip(np.asarray(x, dtype=np.float64), -448.0, 448.0)
-    flat = x.reshape(-1)
-    out = np.empty(flat.shape, dtype=np.uint8)
-    for i, t in enumerate(flat):
-        err = np.abs(fv - t)
-        best = np.flatnonzero(err == err.min())
-        codes = finite[best]
-        if len(codes) > 1:  # a tie between two neighbours (or +0 / -0): the even one
-            even = codes[(codes & 1) == 0]
-            codes = even if len(even) else codes
-            if t >= 0:
-                codes = codes[(codes & 0x80) == 0] if np.any((codes & 0x80) == 0) else codes
-            else:
-                codes = codes[(codes & 0x80) != 0] if np.any((codes & 0x80) != 0) else codes
-        out[i] = codes[0]
-    return out.reshape(x.shape)
+    a = np.abs(x)
+    hi = np.minimum(np.searchsorted(pos, a, side="left"), 0x7E)
+    lo = np.maximum(hi - 1, 0)
+    dl, dh = a - pos[lo], pos[hi] - a
+    pick = np.where(dl < dh, lo, np.where(dh < dl, hi, np.where(lo % 2 == 0, lo, hi)))
+    return (pick | np.where(x < 0, 0x80, 0)).astype(np.uint8)
 
 
 def e4m3_to_f64(c):
@@ -147,4 +138,32 @@ def bf16_centroid_tables(index, q):
             qq = qb[off:off + ln]
             out[i, h] = ((cb - qq[None, :]) ** 2).sum(axis=1)
             norms[i, h] = (qq ** 2).sum() + (cb ** 2).sum(axis=1)
+    return out, norms
+
+
+def fp8_centroid_tables(index, q, data_scales):
+    """Half-subspace squared distances between the E4M3-coded query and the
+    E4M3-coded centroids, in FP64: [Ns][2][sqrtK], and the norms
+    |q_h|^2 + |c|^2 of the coded vectors (the scale of the FP32 error of the
+    tensor-core form |q|^2 - 2<q,c> + |c|^2).  Centroids of subspace i are
+    coded with the dataset's scale data_scales[i]; the query with its own
+    scale t_i = (largest |q| over subspace i) / 448 in FP32 (1 for an all-zero
+    subspace); every code is e4m3 of the FP32 quotient, its value code * scale."""
+    Ns, sk = index["Ns"], index["sqrtK"]
+    cent = np.asarray(index["centroids"], dtype=np.float32)
+    q = np.asarray(q, dtype=np.float32)
+    d = len(q)
+    out = np.empty((Ns, 2, sk), dtype=np.float64)
+    norms = np.empty((Ns, 2, sk), dtype=np.float64)
+    for i in range(Ns):
+        so, sl = _o.subspace_dims(d, Ns, i)
+        m = np.float32(np.abs(q[so:so + sl]).max())
+        t = np.float32(m / np.float32(448.0)) if m > 0 else np.float32(1.0)
+        s = np.float32(data_scales[i])
+        for h in range(2):
+            off, ln = _o.half_dims(d, Ns, i, h)
+            qc = e4m3_to_f64(quantize_e4m3((q[off:off + ln] / t).astype(np.float32).astype(np.float64))) * float(t)
+            cc = e4m3_to_f64(quantize_e4m3((cent[i, h, :, :ln] / s).astype(np.float32).astype(np.float64))) * float(s)
+            out[i, h] = ((cc - qc[None, :]) ** 2).sum(axis=1)
+            norms[i, h] = (qc ** 2).sum() + (cc ** 2).sum(axis=1)
     return out, norms

@@ -535,6 +535,22 @@ ORC_EXPORT int orc_query_batch(const float* X, int64_t n, int32_t d, int32_t Ns,
     return 0;
 }
 
+/* The same with one (T, C) pair per query (per-query alpha and beta). */
+ORC_EXPORT int orc_query_batch_pq(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
+                                  const float* centroids, const int64_t* cell_off, const int64_t* perm, const float* Q,
+                                  int64_t nq, int32_t k, const int64_t* T, const int64_t* C, int32_t rank_precision,
+                                  int32_t nthreads, int64_t* out_ids, double* out_dist)
+{
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t b = 0; b < nq; ++b)
+        orc_query(X, n, d, Ns, sqrtK, centroids, cell_off, perm, Q + (size_t)b * d, k, T[b], C[b], rank_precision,
+                  out_ids + (size_t)b * k, out_dist + (size_t)b * k, NULL, NULL, NULL, NULL, NULL);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1: SC-Linear (no index).  Per subspace, the T points nearest to
  * q in that subspace (sorted by (distance, id)) collide.                     */

@@ -60,6 +60,8 @@ def lib():
     L.orc_query_from_tables.restype = C.c_int
     L.orc_query_batch.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i64, i32, i64, i64,
                                   i32, i32, _i64p, _f64p]
+    L.orc_query_batch_pq.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i64, i32, _i64p, _i64p,
+                                     i32, i32, _i64p, _f64p]
     L.orc_sc_linear.argtypes = [_f32p, i64, i32, i32, _f32p, i32, i64, i64, _i64p, _f64p, vp]
     L.orc_max_threads.restype = C.c_int
     _lib = L
@@ -254,12 +256,20 @@ def query_from_tables(X, index, q, k, T, C_, dtab):
 
 
 def query_batch(X, index, Q, k, T, C_, rank_precision=1, nthreads=1):
+    """Algorithm 4 over a batch, OpenMP over queries.  T and C_ are scalars or
+    one value per query."""
     X = _f32(X)
     Q = _f32(Q)
     n, d = X.shape
     nq = Q.shape[0]
     oi = np.empty((nq, k), dtype=np.int64)
     od = np.empty((nq, k), dtype=np.float64)
+    if np.ndim(T) or np.ndim(C_):
+        Tq = np.ascontiguousarray(np.broadcast_to(np.asarray(T, dtype=np.int64), (nq,)))
+        Cq = np.ascontiguousarray(np.broadcast_to(np.asarray(C_, dtype=np.int64), (nq,)))
+        lib().orc_query_batch_pq(X, n, d, index["Ns"], index["sqrtK"], index["centroids"], index["cell_off"],
+                                 index["perm"], Q, nq, k, Tq, Cq, rank_precision, int(nthreads), oi, od)
+        return oi, od
     lib().orc_query_batch(X, n, d, index["Ns"], index["sqrtK"], index["centroids"], index["cell_off"],
                           index["perm"], Q, nq, k, int(T), int(C_), rank_precision, int(nthreads), oi, od)
     return oi, od

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <unordered_set>
 #include <vector>
@@ -34,10 +35,41 @@ int fail(int code, const char* fmt, ...)
 
 void clear_error() { g_err[0] = 0; }
 
+namespace {
+std::atomic<int32_t> g_fault_kind{SUCO_FAULT_NONE};
+std::atomic<int32_t> g_fault_after{0};
+}  // namespace
+
+bool fault_fires(int32_t kind)
+{
+    if (g_fault_kind.load(std::memory_order_relaxed) != kind) return false;
+    if (g_fault_after.fetch_sub(1) != 0) return false;
+    g_fault_kind.store(SUCO_FAULT_NONE);
+    return true;
+}
+
+int launch_status(const char* what)
+{
+    if (fault_fires(SUCO_FAULT_LAUNCH)) return fail(SUCO_ECUDA, "%s: injected launch failure", what);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(SUCO_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return SUCO_OK;
+}
+
+int check_status(const DeviceIndex* ix)
+{
+    const uint32_t s = ix->status_host ? *ix->status_host : 0u;
+    if (s)
+        return fail(SUCO_ETIMEOUT, "a bounded device wait on this index gave up (status 0x%x): results since then "
+                                   "are unreliable; suco_read_status reads and clears the word", s);
+    return SUCO_OK;
+}
+
 int DevBuf::alloc(size_t b)
 {
     bytes = b;
     if (b == 0) return SUCO_OK;
+    if (fault_fires(SUCO_FAULT_ALLOC)) return fail(SUCO_ENOMEM, "cudaMalloc(%zu): injected allocation failure", b);
     cudaError_t e = cudaMalloc(&p, b);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -73,6 +105,9 @@ void free_index_memory(DeviceIndex* ix)
     cudaFree(ix->rank_ws);
     cudaFree(ix->X8);
     cudaFree(ix->s8col);
+    if (ix->status_host) cudaFreeHost((void*)ix->status_host);
+    ix->status_host = nullptr;
+    ix->status_dev = nullptr;
     ix->X8 = nullptr;
     ix->s8col = nullptr;
     ix->Xh = nullptr;
@@ -123,17 +158,32 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
         {(void**)&ix->cell_off, (size_t)Ns * (ix->K + 1) * 4},
         {(void**)&ix->perm, (size_t)Ns * n * 4 + 16},  // padded: the query scan reads whole 16-byte quads
         {(void**)&ix->split, (size_t)Ns * (ix->nch + 1) * ix->K * 4},
-        {(void**)&ix->work, (size_t)(STATUS_WORD + WORK_STRIDE) * 4},
+        {(void**)&ix->work, (size_t)WORK_SLOTS * WORK_STRIDE * 4},
     };
     ix->bytes = 0;
     for (auto& e : a) {
-        cudaError_t err = cudaMalloc(e.p, e.b);
+        cudaError_t err = fault_fires(SUCO_FAULT_ALLOC) ? cudaErrorMemoryAllocation : cudaMalloc(e.p, e.b);
         if (err != cudaSuccess) {
             cudaGetLastError();
             free_index_memory(ix);
             return fail(SUCO_ENOMEM, "cudaMalloc(%zu) for the index failed: %s", e.b, cudaGetErrorString(err));
         }
         ix->bytes += (int64_t)e.b;
+    }
+    {
+        void* h = nullptr;
+        cudaError_t err = fault_fires(SUCO_FAULT_ALLOC) ? cudaErrorMemoryAllocation
+                                                        : cudaHostAlloc(&h, 4, cudaHostAllocMapped);
+        if (err == cudaSuccess) {
+            ix->status_host = static_cast<volatile uint32_t*>(h);
+            *ix->status_host = 0u;
+            err = cudaHostGetDevicePointer((void**)&ix->status_dev, h, 0);
+        }
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            free_index_memory(ix);
+            return fail(SUCO_ENOMEM, "mapped host allocation of the status word failed: %s", cudaGetErrorString(err));
+        }
     }
     SUCO_CUDA_TRY(cudaMemsetAsync(ix->cent, 0, a[1].b, st));
     SUCO_CUDA_TRY(cudaMemsetAsync(ix->work, 0, a[5].b, st));
@@ -161,11 +211,15 @@ int check_query_params(const suco_index* index, const float* queries, int64_t nq
     if (p->precision == SUCO_PRECISION_FP8 && !index->ix.X8)
         return fail(SUCO_ESTATE, "the index has no FP8 copy: call suco_add_reduced_copies first");
     if (p->id_passes < 0) return fail(SUCO_EINVAL, "id_passes=%d must not be negative", p->id_passes);
-    if (p->rank_precision != SUCO_RANK_FP32 && p->rank_precision != SUCO_RANK_BF16)
-        return fail(SUCO_EINVAL, "rank_precision=%d must be SUCO_RANK_FP32 or SUCO_RANK_BF16", p->rank_precision);
-    if (p->rank_precision == SUCO_RANK_BF16 && !index->ix.rank_ws)
-        return fail(SUCO_ESTATE, "BF16 ranking needs its tables workspace: call suco_add_reduced_copies with "
+    if (p->rank_precision != SUCO_RANK_FP32 && p->rank_precision != SUCO_RANK_BF16 &&
+        p->rank_precision != SUCO_RANK_FP8)
+        return fail(SUCO_EINVAL, "rank_precision=%d must be SUCO_RANK_FP32, _BF16 or _FP8", p->rank_precision);
+    if (p->rank_precision != SUCO_RANK_FP32 && !index->ix.rank_ws)
+        return fail(SUCO_ESTATE, "tensor-core ranking needs its tables workspace: call suco_add_reduced_copies with "
                                  "SUCO_COPY_RANK_BF16 first");
+    if (p->rank_precision == SUCO_RANK_FP8 && !index->ix.s8col)
+        return fail(SUCO_ESTATE, "FP8 ranking uses the scales of the FP8 copy: call suco_add_reduced_copies with "
+                                 "SUCO_COPY_FP8 first");
     if (p->exact_rerank < 0 || p->exact_rerank > (1 << 24))
         return fail(SUCO_EINVAL, "exact_rerank=%d must be in [0, 2^24]", p->exact_rerank);
     if (nq > 0 && (!queries || !ids || !dist)) return fail(SUCO_EINVAL, "queries/out_ids/out_dist must not be NULL");
@@ -215,7 +269,7 @@ int suco_build_index(const float* data, int64_t n, int32_t d, const suco_build_p
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
-    suco_index* idx = new (std::nothrow) suco_index();
+    suco_index* idx = fault_fires(SUCO_FAULT_ALLOC) ? nullptr : new (std::nothrow) suco_index();
     if (!idx) return fail(SUCO_ENOMEM, "host allocation failed");
     rc = alloc_index(&idx->ix, data, n, d, Ns, sk, st);
     if (!rc) rc = kmeans_build(&idx->ix, init.data(), params->kmeans_iters, st);
@@ -241,7 +295,7 @@ int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, i
         if (assign[t] < 0 || assign[t] >= sqrtK)
             return fail(SUCO_EINVAL, "assign[%lld] = %d out of [0, %d)", (long long)t, assign[t], sqrtK);
     cudaStream_t st = (cudaStream_t)stream;
-    suco_index* idx = new (std::nothrow) suco_index();
+    suco_index* idx = fault_fires(SUCO_FAULT_ALLOC) ? nullptr : new (std::nothrow) suco_index();
     if (!idx) return fail(SUCO_ENOMEM, "host allocation failed");
     DeviceIndex* ix = &idx->ix;
     rc = alloc_index(ix, data, n, d, Ns, sqrtK, st);
@@ -282,6 +336,7 @@ int suco_query_batch(const suco_index* index, const float* queries, int64_t nq, 
     clear_error();
     int rc = check_query_params(index, queries, nq, params, out_ids, out_dist);
     if (rc) return rc;
+    if ((rc = check_status(&index->ix))) return rc;
     return launch_query(&index->ix, queries, nq, params, out_ids, out_dist, nullptr, (cudaStream_t)stream);
 }
 
@@ -291,6 +346,7 @@ int suco_query_debug(const suco_index* index, const float* queries, int64_t nq, 
     clear_error();
     int rc = check_query_params(index, queries, nq, params, out_ids, out_dist);
     if (rc) return rc;
+    if ((rc = check_status(&index->ix))) return rc;
     return launch_query(&index->ix, queries, nq, params, out_ids, out_dist, debug, (cudaStream_t)stream);
 }
 
@@ -395,10 +451,22 @@ int suco_read_status(suco_index* index, uint32_t* status)
 {
     clear_error();
     if (!index || !status) return fail(SUCO_EINVAL, "index and status must not be NULL");
-    uint32_t* word = index->ix.work + STATUS_WORD;
     SUCO_CUDA_TRY(cudaDeviceSynchronize());
-    SUCO_CUDA_TRY(cudaMemcpy(status, word, 4, cudaMemcpyDeviceToHost));
-    SUCO_CUDA_TRY(cudaMemset(word, 0, 4));
+    *status = *index->ix.status_host;
+    *index->ix.status_host = 0u;
+    return SUCO_OK;
+}
+
+int suco_inject_fault(int32_t kind, int32_t after)
+{
+    clear_error();
+    if (kind != SUCO_FAULT_NONE && kind != SUCO_FAULT_ALLOC && kind != SUCO_FAULT_LAUNCH &&
+        kind != SUCO_FAULT_WAIT_TIMEOUT)
+        return fail(SUCO_EINVAL, "unknown fault kind %d", kind);
+    if (after < 0) return fail(SUCO_EINVAL, "after=%d must not be negative", after);
+    g_fault_kind.store(SUCO_FAULT_NONE);
+    g_fault_after.store(after);
+    g_fault_kind.store(kind);
     return SUCO_OK;
 }
 

@@ -247,18 +247,18 @@ int build_imi(DeviceIndex* ix, const int32_t* assign, cudaStream_t st)
     for (int i = 0; i < ix->Ns; ++i) {
         cells_kernel<<<grid_for(n, 256), 256, 0, st>>>(assign + (int64_t)(2 * i) * n, assign + (int64_t)(2 * i + 1) * n,
                                                        n, ix->sqrtK, cells.as<uint32_t>(), iota.as<int32_t>());
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("cells_kernel");
         size_t tb = tmp_bytes;
         SUCO_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tb, cells.as<uint32_t>(), sorted.as<uint32_t>(),
                                                       iota.as<int32_t>(), ix->perm + (int64_t)i * n, (int)n, 0,
                                                       end_bit, st));
         cell_off_kernel<<<grid_for(K + 1, 256), 256, 0, st>>>(sorted.as<uint32_t>(), n, K,
                                                               ix->cell_off + (int64_t)i * (K + 1));
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("cell_off_kernel");
     }
     split_kernel<<<grid_for((int64_t)ix->Ns * (ix->nch + 1) * K, 256), 256, 0, st>>>(
         ix->cell_off, ix->perm, n, ix->Ns, K, ix->n_ch, ix->nch, ix->split);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("split_kernel");
     SUCO_CUDA_TRY(cudaStreamSynchronize(st));
     return SUCO_OK;
 }
@@ -275,13 +275,13 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
     SUCO_CUDA_TRY(cudaMemcpyAsync(ids.p, init_ids_host, (size_t)H * sk * 8, cudaMemcpyHostToDevice, st));
     init_centroids_kernel<<<dim3(grid_for((int64_t)sk * hm, 256), H), 256, 0, st>>>(ix->X, ix->ld, ix->d, Ns, ix->sub_s,
                                                                                    sk, hm, ids.as<int64_t>(), ix->cent);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("init_centroids_kernel");
 
     // fixed-point scale per half: max|x| * 2^S * n < 2^62
     SUCO_CUDA_TRY(cudaMemsetAsync(maxabs.p, 0, (size_t)H * 4, st));
     maxabs_kernel<<<dim3(grid_for(n, 256, 1024), H), 256, 0, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s,
                                                                    maxabs.as<unsigned>());
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("maxabs_kernel");
     std::vector<unsigned> mbits(H);
     SUCO_CUDA_TRY(cudaMemcpyAsync(mbits.data(), maxabs.p, (size_t)H * 4, cudaMemcpyDeviceToHost, st));
     SUCO_CUDA_TRY(cudaStreamSynchronize(st));
@@ -324,22 +324,22 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
     for (int it = 0; it < iters; ++it) {
         kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm,
                                                                 ix->cent, assign.as<int32_t>());
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
         SUCO_CUDA_TRY(cudaMemsetAsync(gsum.p, 0, gsum.bytes, st));
         SUCO_CUDA_TRY(cudaMemsetAsync(gcnt.p, 0, gcnt.bytes, st));
         kmeans_accum_kernel<<<g_accum, 256, use_smem ? accum_smem : 0, st>>>(
             ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm, assign.as<int32_t>(), scale.as<float>(),
             gsum.as<unsigned long long>(), gcnt.as<unsigned>(), use_smem);
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("kmeans_accum_kernel");
         kmeans_finalize_kernel<<<dim3(grid_for((int64_t)sk * max_len, 256), H), 256, 0, st>>>(
             ix->d, Ns, ix->sub_s, sk, hm, gsum.as<unsigned long long>(), gcnt.as<unsigned>(), inv_scale.as<float>(),
             ix->cent);
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("kmeans_finalize_kernel");
     }
     // the assignment that defines the IMI, against the final centroids
     kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm, ix->cent,
                                                             assign.as<int32_t>());
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
     return build_imi(ix, assign.as<int32_t>(), st);
 }
 
@@ -425,7 +425,7 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
     // fixed-point scale: max|x| * 2^S * n < 2^62
     SUCO_CUDA_TRY(cudaMemsetAsync(maxabs, 0, 4, st));
     maxabs_kernel<<<dim3(grid_for(n, 256, 1024), 1), 256, 0, st>>>(Xc, d, n, dd, 1, sub, maxabs);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("maxabs_kernel");
     unsigned mbits = 0;
     SUCO_CUDA_TRY(cudaMemcpyAsync(&mbits, maxabs, 4, cudaMemcpyDeviceToHost, st));
     SUCO_CUDA_TRY(cudaStreamSynchronize(st));
@@ -451,19 +451,19 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
     const dim3 g_accum(grid_for(n, 256, 2 * nsm), 1);
     for (int it = 0; it < iters; ++it) {
         kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign);
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
         // sums and counts start from zero in every iteration (the array keeps the last call's contents)
         SUCO_CUDA_TRY(cudaMemsetAsync(gsum, 0, (size_t)k * dim_len * 8, st));
         SUCO_CUDA_TRY(cudaMemsetAsync(gcnt, 0, (size_t)k * 4, st));
         kmeans_accum_kernel<<<g_accum, 256, use_smem ? accum_smem : 0, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, assign,
                                                                              scale, gsum, gcnt, use_smem);
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("kmeans_accum_kernel");
         kmeans_finalize_kernel<<<dim3(grid_for((int64_t)k * dim_len, 256), 1), 256, 0, st>>>(
             dd, 1, sub, k, dim_len, gsum, gcnt, inv_scale, centroids);
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("kmeans_finalize_kernel");
     }
     // the assignment against the final centroids
     kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
     return SUCO_OK;
 }

@@ -20,9 +20,7 @@ namespace suco {
 constexpr int WORK_SLOTS = 64;
 constexpr int WORK_STRIDE = 8;  // 32 bytes per slot
 constexpr int MIN_NCH = 64;
-// device status word after the work counters: bit 0 = a kernel's bounded wait gave up
-constexpr int STATUS_WORD = WORK_SLOTS * WORK_STRIDE;
-// queries per launch pair of the BF16 tensor-core ranking (tables workspace rows)
+// queries per launch pair of the tensor-core ranking (tables workspace rows)
 constexpr int64_t RANK_CHUNK = 4096;
 constexpr int64_t MAX_CHUNK = 1 << 17;
 
@@ -39,7 +37,7 @@ struct DeviceIndex {
     int32_t nch = 0;    // chunks
     float* X = nullptr;           // [n][ld]; columns d..ld-1 are zero
     uint16_t* Xh = nullptr;       // optional BF16 copy of X, [n][ldh] (ldh = d rounded up to 8), padding zero
-    float* rank_ws = nullptr;     // optional [RANK_CHUNK][Ns][2][sqrtK] centroid-distance tables (BF16 ranking)
+    float* rank_ws = nullptr;     // optional [RANK_CHUNK][Ns][2][sqrtK] centroid-distance tables (tensor-core ranking)
     uint8_t* X8 = nullptr;        // optional FP8 E4M3 copy of X / scale, [n][ld8] (ld8 = d rounded up to 16)
     float* s8col = nullptr;       // [ld8] scale of every column (its subspace's), 0 past d
     int64_t ld8 = 0;
@@ -54,6 +52,11 @@ struct DeviceIndex {
     // may be in flight at once
     uint32_t* work = nullptr;
     uint32_t work_next = 0;
+    // status word in mapped (pinned) host memory: a kernel whose bounded wait
+    // gives up stores SUCO_STATUS_WAIT_TIMEOUT through status_dev; the host
+    // reads status_host without synchronising
+    volatile uint32_t* status_host = nullptr;
+    uint32_t* status_dev = nullptr;
     int device = 0;
     int64_t bytes = 0;
     // launch shapes chosen by suco_autotune, per (k, candidate bound C)
@@ -81,6 +84,14 @@ __host__ __device__ inline void half_dims(int32_t d, int32_t Ns, int32_t sub_s, 
 int fail(int code, const char* fmt, ...);
 void clear_error();
 
+// Failure injection (suco_inject_fault): true when an armed fault of this
+// kind fires now (it then disarms itself).
+bool fault_fires(int32_t kind);
+// After a kernel launch: an injected launch fault, or the launch's own error.
+int launch_status(const char* what);
+// A status word set by a kernel's bounded wait (or by an injected fault).
+int check_status(const DeviceIndex* ix);
+
 // Device memory with automatic release.
 struct DevBuf {
     void* p = nullptr;
@@ -93,7 +104,7 @@ struct DevBuf {
 
 int build_imi(DeviceIndex* ix, const int32_t* assign_dev /*[Ns][2][n]*/, cudaStream_t st);
 int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, cudaStream_t st);
-int rank_bf16_tables(const DeviceIndex* ix, const float* Q, int64_t nq, float* D, cudaStream_t st);
+int rank_tc_tables(const DeviceIndex* ix, const float* Q, int64_t nq, float* D, bool fp8, cudaStream_t st);
 int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_query_params* p, int32_t* ids,
                  float* dist, const suco_query_debug_out* dbg, cudaStream_t st);
 
@@ -104,6 +115,12 @@ void thresholds(int64_t n, double alpha, double beta, int32_t k, int64_t* T, int
 struct suco_index {
     suco::DeviceIndex ix;
 };
+
+#define SUCO_LAUNCH_CHECK(what)                      \
+    do {                                             \
+        int rc_ = ::suco::launch_status(what);       \
+        if (rc_) return rc_;                         \
+    } while (0)
 
 #define SUCO_CUDA_TRY(expr)                                                                          \
     do {                                                                                             \

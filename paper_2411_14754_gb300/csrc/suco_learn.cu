@@ -346,7 +346,7 @@ int suco_query_features(const suco_index* index, const float* queries, int64_t n
     SUCO_CUDA_TRY(cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     features_kernel<<<(unsigned)nq, 128, smem, (cudaStream_t)stream>>>(ix.cent, ix.cell_off, ix.d, ix.Ns, ix.sub_s,
                                                                       ix.sqrtK, ix.hmax, ix.K, queries, nq, feats);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("features_kernel");
     return SUCO_OK;
 }
 
@@ -370,7 +370,7 @@ int suco_mlp_predict(const suco_index* index, const suco_mlp* model, const float
         M, ix.cent, ix.cell_off, ix.d, ix.Ns, ix.sub_s, ix.sqrtK, ix.hmax, ix.K, queries, nq, model->out_offset[0],
         model->out_offset[1], model->log_alpha_min, model->log_alpha_max, model->log_beta_min, model->log_beta_max,
         model->fallback_alpha, model->fallback_beta, alpha, beta, nullptr);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("predict_kernel");
     return SUCO_OK;
 }
 
@@ -386,7 +386,7 @@ int suco_mlp_forward(const suco_mlp* model, const float* x, int64_t B, float* z1
     const size_t smem = 4ull * warps * M.F;
     mlp_forward_kernel<<<(unsigned)((B + warps - 1) / warps), 32 * warps, smem, (cudaStream_t)stream>>>(M, x, B, z1, h,
                                                                                                         y);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("mlp_forward_kernel");
     return SUCO_OK;
 }
 
@@ -405,11 +405,11 @@ int suco_mlp_backward(const suco_mlp* model, const float* x, int64_t B, const fl
     const int warps = 8;
     mlp_backward_z_kernel<<<(unsigned)((B + warps - 1) / warps), 32 * warps, 0, st>>>(M, y, target, B, z1, dy, dz1,
                                                                                        loss);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("mlp_backward_z_kernel");
     mlp_backward_w1_kernel<<<grid1((int64_t)(M.F + 1) * M.H, 128), 128, 0, st>>>(M, x, B, dz1, dw1, db1);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("mlp_backward_w1_kernel");
     mlp_backward_w2_kernel<<<grid1((M.H + 1) * 2, 128), 128, 0, st>>>(M, h, dy, B, dw2, db2);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("mlp_backward_w2_kernel");
     return SUCO_OK;
 }
 
@@ -422,7 +422,7 @@ int suco_adamw_step(float* param, const float* grad, float* m, float* v, int64_t
     const float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
     adamw_kernel<<<grid1(count, 256), 256, 0, (cudaStream_t)stream>>>(param, grad, m, v, count, lr, beta1, beta2, eps,
                                                                       weight_decay, bc1, bc2, bf16_copy);
-    SUCO_CUDA_TRY(cudaGetLastError());
+    SUCO_LAUNCH_CHECK("adamw_kernel");
     return SUCO_OK;
 }
 

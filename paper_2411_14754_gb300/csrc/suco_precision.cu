@@ -98,7 +98,7 @@ extern "C" int suco_add_reduced_copies(suco_index* index, int32_t mask, void* st
         const int64_t work = ix->n * (ldh / 8);
         const int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
         to_bf16_kernel<<<grid, 256, 0, st>>>(ix->X, ix->ld, ix->n, ix->d, b.as<uint16_t>(), ldh);
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("to_bf16_kernel");
         SUCO_CUDA_TRY(cudaStreamSynchronize(st));
         ix->Xh = b.as<uint16_t>();
         ix->ldh = ldh;
@@ -116,7 +116,7 @@ extern "C" int suco_add_reduced_copies(suco_index* index, int32_t mask, void* st
         const int gx = (int)std::min<int64_t>((ix->n + 255) / 256, 1024);
         subspace_maxabs_kernel<<<dim3(gx, ix->Ns), 256, 0, st>>>(ix->X, ix->ld, ix->n, ix->d, ix->Ns, ix->sub_s,
                                                                  mx.as<unsigned>());
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("subspace_maxabs_kernel");
         std::vector<unsigned> mbits(ix->Ns);
         SUCO_CUDA_TRY(cudaMemcpyAsync(mbits.data(), mx.p, (size_t)ix->Ns * 4, cudaMemcpyDeviceToHost, st));
         SUCO_CUDA_TRY(cudaStreamSynchronize(st));
@@ -134,7 +134,7 @@ extern "C" int suco_add_reduced_copies(suco_index* index, int32_t mask, void* st
         const int64_t work = ix->n * (ld8 / 16);
         const int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
         to_fp8_kernel<<<grid, 256, 0, st>>>(ix->X, ix->ld, ix->n, ix->d, cs.as<float>(), b.as<uint8_t>(), ld8);
-        SUCO_CUDA_TRY(cudaGetLastError());
+        SUCO_LAUNCH_CHECK("to_fp8_kernel");
         SUCO_CUDA_TRY(cudaStreamSynchronize(st));
         ix->X8 = b.as<uint8_t>();
         ix->s8col = cs.as<float>();

@@ -2088,6 +2088,7 @@ int launch_t(const Layout& L, int64_t nq, bool persistent, uint32_t* work, cudaS
         if (G < nq) A.work = work;
     }
     cfg.gridDim = dim3((unsigned)(G * L.A.CL), 1, 1);
+    if (fault_fires(SUCO_FAULT_LAUNCH)) return fail(SUCO_ECUDA, "suco_query_kernel: injected launch failure");
     SUCO_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, A));
     return SUCO_OK;
 }
@@ -2212,12 +2213,13 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
         A.dbg_surv = dbg->survivors;
     }
     const bool persistent = (p->flags & SUCO_QUERY_ONE_CLUSTER_PER_QUERY) == 0;
-    if (p->rank_precision == SUCO_RANK_BF16) {
+    if (p->rank_precision == SUCO_RANK_BF16 || p->rank_precision == SUCO_RANK_FP8) {
         // one tensor-core table launch and one query launch per RANK_CHUNK queries
         const QArgs base = A;
         for (int64_t c0 = 0; c0 < nq; c0 += RANK_CHUNK) {
             const int64_t cnt = std::min<int64_t>(RANK_CHUNK, nq - c0);
-            int rc = rank_bf16_tables(ix, Q + c0 * ix->d, cnt, ix->rank_ws, st);
+            int rc = rank_tc_tables(ix, Q + c0 * ix->d, cnt, ix->rank_ws, p->rank_precision == SUCO_RANK_FP8, st);
+            if (!rc) rc = check_status(ix);  // a wait that gave up is reported before its tables are used
             if (rc) return rc;
             QArgs& C2 = L.A;
             C2 = base;

@@ -133,6 +133,9 @@ class Mlp:
     seed: int = 0
     offsets: Sequence[float] = (0.0, 0.0)
     tensors: dict = field(default_factory=dict)
+    # held-out training queries that choose operating points (set by fit):
+    # Q (device tensor), gt (exact k-NN ids)
+    validation: dict = field(default_factory=dict)
 
     def __post_init__(self):
         rng = np.random.default_rng(self.seed)
@@ -311,6 +314,7 @@ def fit(index: S.SucoIndex, Xd: torch.Tensor, Qtrain: torch.Tensor, k: int, val_
     Qv, gv = Qtrain[ntr:].contiguous(), gt[ntr:]
     margin, r = tune_offsets(index, model, Qv, gv, k, target=target)
     model.offsets = (margin, margin)
+    model.validation = dict(Q=Qv.clone(), gt=gv)
     alpha, beta = predict(index, model, Qv)
     a_np, b_np = alpha.cpu().numpy().astype(np.float64), beta.cpu().numpy().astype(np.float64)
     learned_bytes = float(np.mean(path_bytes(a_np, b_np, index.n, index.d, index.Ns)))

@@ -85,13 +85,15 @@ def load_library():
                                   i32, vp, vp]
     L.suco_add_reduced_copies.argtypes = [vp, i32, vp]
     L.suco_read_status.argtypes = [vp, C.POINTER(C.c_uint32)]
+    L.suco_inject_fault.argtypes = [i32, i32]
     L.suco_free.argtypes = [vp]
     L.suco_free.restype = None
     L.suco_last_error.restype = C.c_char_p
     for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_query_batch", "suco_query_debug",
                  "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version",
                  "suco_kmeans_noalloc", "suco_autotune", "suco_query_features", "suco_mlp_predict",
-                 "suco_mlp_forward", "suco_mlp_backward", "suco_adamw_step", "suco_add_reduced_copies", "suco_read_status"):
+                 "suco_mlp_forward", "suco_mlp_backward", "suco_adamw_step", "suco_add_reduced_copies", "suco_read_status",
+                 "suco_inject_fault"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -194,7 +196,7 @@ def _per_query(t, dtype, nq, name):
 QUERY_ONE_CLUSTER_PER_QUERY = 1
 
 
-PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}  # also the rank_precision codes (SUCO_RANK_*)
 COPY_BF16, COPY_RANK_BF16, COPY_FP8 = 1, 2, 4
 
 
@@ -376,6 +378,15 @@ def suco_read_status(index: SucoIndex) -> int:
     st = C.c_uint32(0)
     _check(load_library().suco_read_status(index.handle, C.byref(st)))
     return int(st.value)
+
+
+FAULT_NONE, FAULT_ALLOC, FAULT_LAUNCH, FAULT_WAIT_TIMEOUT = 0, 1, 2, 3
+
+
+def suco_inject_fault(kind: int, after: int = 0):
+    """Arm one host-side fault (test hook): the after-th allocation, kernel
+    launch or tensor-core ranking wait from now fails (see include/suco.h)."""
+    _check(load_library().suco_inject_fault(int(kind), int(after)))
 
 
 def suco_last_error() -> str:

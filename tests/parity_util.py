@@ -2,9 +2,12 @@
 import numpy as np
 
 import oracle
+from oracle import precision_oracle as P
 
 # FP32 re-rank distances against the FP64 oracle (tolerance of the FP32 path)
 RTOL = 1e-5
+# FP32 sum of d non-negative terms vs FP64, relative, at the R-th coarse distance
+COARSE_RTOL = 2e-5
 
 
 def true_sqdist(X, q, ids):
@@ -59,3 +62,30 @@ def check_query_against_oracle(X, idx_o, q, gpu, b, k, T, C, stages=True):
             assert sorted(gc.tolist()) == sorted(o["cands"].tolist())
     assert_topk_matches(X, q, gpu["ids"][b], gpu["dist"][b], o["ids"], o["dist"])
     return o
+
+
+def check_coarse_against_oracle(X, q, gpu_cands, gpu_surv, gpu_ids, gpu_dist, o_cands, k, R, prec, Ns=None,
+                                scales=None):
+    """One query of the BF16/FP8 coarse re-rank vs the reduced-precision oracle.
+    gpu_cands: the GPU's candidate ids; gpu_surv: ids flagged as survivors;
+    o_cands: the oracle's candidates (same set).  The survivors must be the R
+    candidates with the smallest (coarse distance, id), up to candidates whose
+    coarse distance ties the R-th within FP32 rounding; the result must be the
+    exact top-k of the GPU's own survivors.  Returns the oracle's coarse pass."""
+    cands = np.asarray(o_cands, dtype=np.int64)
+    C = len(cands)
+    assert sorted(np.asarray(gpu_cands).tolist()) == sorted(cands.tolist())
+    rows = P.decoded_rows(X[cands], 1) if prec == "bf16" else P.decoded_rows(X[cands], 2, Ns, scales)
+    ref = P.coarse_rerank(X, rows, q, cands, R, k)
+    g_surv = np.asarray(gpu_surv, dtype=np.int64)
+    if C > R:
+        assert len(g_surv) == R
+        coarse = dict(zip(cands.tolist(), ref["coarse"].tolist()))
+        cR = np.sort(ref["coarse"])[R - 1]
+        for i in set(g_surv.tolist()) ^ set(ref["survivors"].tolist()):
+            assert abs(coarse[i] - cR) <= COARSE_RTOL * max(cR, 1e-30), (i, coarse[i], cR)
+        ids_s, dist_s = oracle.rerank(X, q, g_surv, k)
+    else:
+        ids_s, dist_s = oracle.rerank(X, q, cands, k)
+    assert_topk_matches(X, q, gpu_ids, gpu_dist, ids_s, dist_s)
+    return ref

@@ -101,3 +101,26 @@ def test_noalloc_assign_output_is_checked_before_any_launch():
     with pytest.raises(ValueError):
         S._same_device(torch.empty(3, device="meta"), torch.empty(3), "centroids")
     S._same_device(torch.empty(3), torch.empty(3), "centroids")
+
+
+def test_fault_injection_on_the_host_without_a_gpu(lib):
+    # an injected failure of the host index allocation is reported before the
+    # library touches the device: suco_build_index returns SUCO_ENOMEM
+    lib.suco_last_error.restype = ctypes.c_char_p
+    lib.suco_inject_fault.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    assert lib.suco_inject_fault(9, 0) == -1
+    assert lib.suco_inject_fault(1, -1) == -1
+
+    class Params(ctypes.Structure):
+        _fields_ = [("Ns", ctypes.c_int32), ("sqrtK", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32),
+                    ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64), ("init_ids", ctypes.c_void_p)]
+
+    lib.suco_build_index.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Params),
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    out = ctypes.c_void_p()
+    p = Params(2, 4, 1, 0, 7, None)
+    assert lib.suco_inject_fault(1, 0) == 0                       # SUCO_FAULT_ALLOC, the next allocation
+    rc = lib.suco_build_index(ctypes.c_void_p(16), 100, 8, ctypes.byref(p), None, ctypes.byref(out))
+    assert rc == -2 and out.value is None
+    assert b"injected" in lib.suco_last_error() or b"host allocation" in lib.suco_last_error()
+    assert lib.suco_inject_fault(0, 0) == 0                       # disarm

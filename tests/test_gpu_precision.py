@@ -17,12 +17,9 @@ import oracle
 import paper_2411_14754_gb300 as pkg
 from oracle import precision_oracle as P
 from paper_2411_14754_gb300 import workloads as W
-from parity_util import assert_topk_matches
+from parity_util import check_coarse_against_oracle
 
 pytestmark = pytest.mark.gpu
-
-COARSE_RTOL = 2e-5  # FP32 sum of d non-negative terms vs FP64, relative, at the R-th coarse distance
-
 
 @pytest.fixture(scope="module", autouse=True)
 def built():
@@ -61,23 +58,8 @@ def check_bf16(X, idx_o, Q, k, alpha, beta, R, cluster_size=0, threads=0, prec="
     T, C = host["T"], host["C"]
     for b in range(len(Q)):
         o = oracle.query(X, idx_o, Q[b], k, T, C, rank_precision=1, debug=True)
-        cands = o["cands"]
-        assert sorted(host["cands"][b].tolist()) == sorted(cands.tolist())
-        rows = P.decoded_rows(X[cands], 1) if prec == "bf16" else P.decoded_rows(X[cands], 2, idx_o["Ns"], scales)
-        ref = P.coarse_rerank(X, rows, Q[b], cands, R, k)
-        g_surv = np.flatnonzero(host["survivors"][b])
-        assert len(g_surv) == min(R, C) if C > R else True
-        if C > R:
-            assert len(g_surv) == R
-            coarse = dict(zip(cands.tolist(), ref["coarse"].tolist()))
-            cR = np.sort(ref["coarse"])[R - 1]
-            for i in set(g_surv.tolist()) ^ set(ref["survivors"].tolist()):
-                assert abs(coarse[i] - cR) <= COARSE_RTOL * max(cR, 1e-30), (b, i, coarse[i], cR)
-            # the final top-k is the exact top-k of the GPU's survivors
-            ids_s, dist_s = oracle.rerank(X, Q[b], g_surv.astype(np.int64), k)
-        else:
-            ids_s, dist_s = oracle.rerank(X, Q[b], cands, k)
-        assert_topk_matches(X, Q[b], host["ids"][b], host["dist"][b], ids_s, dist_s)
+        check_coarse_against_oracle(X, Q[b], host["cands"][b], np.flatnonzero(host["survivors"][b]),
+                                    host["ids"][b], host["dist"][b], o["cands"], k, R, prec, idx_o["Ns"], scales)
     return host
 
 

@@ -391,6 +391,13 @@ def test_batch_driver_matches_single_queries():
         o = oracle.query(X, idx, Q[b], 7, T=75, C_=30, debug=False)
         assert ids[b].tolist() == o["ids"].tolist()
         np.testing.assert_array_equal(dist[b], o["dist"])
+    # one (T, C) per query
+    Ts, Cs = [40, 75, 120, 75, 300, 9], [30, 12, 60, 7, 90, 25]
+    ids, dist = oracle.query_batch(X, idx, Q, 7, T=Ts, C_=Cs, nthreads=3)
+    for b in range(6):
+        o = oracle.query(X, idx, Q[b], 7, T=Ts[b], C_=Cs[b], debug=False)
+        assert ids[b].tolist() == o["ids"].tolist()
+        np.testing.assert_array_equal(dist[b], o["dist"])
 
 
 # ---------------------------------------------------------------------------

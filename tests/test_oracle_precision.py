@@ -130,3 +130,54 @@ def test_bf16_centroid_tables_round_both_operands_like_torch():
             cb = torch.from_numpy(np.ascontiguousarray(idx["centroids"][i, h, :, :ln])).to(torch.bfloat16).double()
             ref = ((cb.numpy() - qb[off:off + ln][None, :]) ** 2).sum(axis=1)
             np.testing.assert_allclose(tab[i, h], ref, rtol=1e-14, atol=0)
+
+
+def test_fp8_centroid_tables_on_e4m3_exact_data_are_the_fp64_distances():
+    # data whose every value is a small integer times 2^-3, a scale that
+    # divides exactly: with the data scale and the query scale chosen so that
+    # every quotient is an E4M3 value, the codes are exact and the tables are
+    # the FP64 squared distances of the raw half-vectors
+    from scipy.spatial.distance import cdist
+    from paper_2411_14754_gb300 import workloads as W
+    n, d, Ns, sk = 1200, 16, 2, 5
+    rng = np.random.default_rng(47)
+    X = (rng.integers(0, 8, size=(n, d)) * 0.125).astype(np.float32)
+    X[0, :] = 0.875                                # max|x| = 7/8 in every subspace
+    idx = oracle.build_index(X, Ns, sk, 0, W.random_init_ids(48, n, Ns, sk))
+    s = P.subspace_scales_e4m3(X, Ns)              # (7/8) / 448 = 2^-9: quotients x * 2^9 are exact
+    assert (s == np.float32(2.0 ** -9)).all()
+    for q in (rng.integers(0, 8, size=(3, d)) * 0.125).astype(np.float32):
+        q[[0, 8]] = 0.875                          # the query's scale is 2^-9 too
+        tab, norms = P.fp8_centroid_tables(idx, q, s)
+        for i in range(Ns):
+            for h in range(2):
+                off, ln = oracle.half_dims(d, Ns, i, h)
+                c = idx["centroids"][i, h, :, :ln].astype(np.float64)
+                qh = q[off:off + ln].astype(np.float64)
+                np.testing.assert_array_equal(tab[i, h], cdist(qh[None, :], c, "sqeuclidean")[0])
+                np.testing.assert_array_equal(norms[i, h], np.dot(qh, qh) + np.einsum("ij,ij->i", c, c))
+
+
+def test_fp8_centroid_tables_code_both_operands_like_torch():
+    # general data: values are torch's float8_e4m3fn casts of the FP32
+    # quotients (a library conversion; no saturation is reached here) times the scales
+    from paper_2411_14754_gb300 import workloads as W
+    n, d, Ns, sk = 1500, 30, 3, 6
+    X = np.abs(W.random_data(49, n, d, kind="gauss")) * np.float32(5.0)
+    idx = oracle.build_index(X, Ns, sk, 2, W.random_init_ids(50, n, Ns, sk))
+    s = P.subspace_scales_e4m3(X, Ns)
+    q = np.abs(W.random_data(51, 1, d, kind="gauss")[0]) * np.float32(5.0)
+    tab, _ = P.fp8_centroid_tables(idx, q, s)
+
+    def coded(v, scale):
+        quot = torch.from_numpy(np.ascontiguousarray(v / np.float32(scale), dtype=np.float32))
+        return quot.to(torch.float8_e4m3fn).double().numpy() * float(scale)
+
+    for i in range(Ns):
+        so, sl = oracle.subspace_dims(d, Ns, i)
+        t = np.float32(np.abs(q[so:so + sl]).max() / np.float32(448.0))
+        for h in range(2):
+            off, ln = oracle.half_dims(d, Ns, i, h)
+            qc = coded(q[off:off + ln], t)
+            cc = coded(idx["centroids"][i, h, :, :ln], s[i])
+            np.testing.assert_allclose(tab[i, h], ((cc - qc[None, :]) ** 2).sum(1), rtol=1e-14, atol=0)
