@@ -189,6 +189,17 @@ typedef struct suco_query_debug_out {
                             scoring above the cut and the lowest-id ties at the cut       */
     uint8_t* survivors;  /* (device) [nq][n], zeroed by the caller: set to 1 for every
                             candidate that survives the BF16/FP8 coarse pass                */
+    int64_t* stage_clock; /* (device) [nq][16][20]: row r is CTA r of the query's cluster
+                            (rows past the cluster size are not written).  Slot 0: the
+                            SM id; slots 1..16: the SM clock (clock64) of thread 0 at the
+                            start of the query, after S0, after S1-S3, after cluster
+                            barrier 1, at the start of S4, after the S4 scan, after the
+                            SC-scores' bit planes, before and after cluster barrier 2,
+                            after the candidate cut, before and after cluster barrier 3,
+                            after the S6 distances, before and after cluster barrier 4,
+                            after the merge (CTA 0 only); slots 18, 19: S4 cycles spent
+                            listing segments and scanning them.  With several passes over
+                            the id range, slots 6-12 hold the last pass. */
 } suco_query_debug_out;
 
 /* suco_query_batch plus the per-stage outputs above (same arguments). */

@@ -57,6 +57,7 @@ constexpr int MAXSEG = 512;   // retrieved-cell segments listed per scan round
 constexpr int NB = 1024;      // linear value buckets of the cut search
 constexpr int MCAP = 1024;    // cells of the crossing bucket resolved from a list
 constexpr int SCAN_U = 3;     // 16-byte quads of ids in flight per lane in the scan
+constexpr int NCLK = 20;      // per-stage clock stamps per (query, CTA) of the debug output
 
 constexpr int S3_BYTES = 4 * NB + 12 * MCAP;  // S3 scratch at the start of the union region
 constexpr int HIST_WORDS = 256 + 64;          // o_hist per S3 group: a 256-bin histogram, scan scratch
@@ -110,6 +111,7 @@ struct QArgs {
     float* dbg_dtab;
     uint8_t* dbg_scores;
     int32_t* dbg_cands;
+    long long* dbg_clk;  // [nq][16][NCLK] per-stage clock64 stamps, row r = CTA r (debug)
     // shared-memory layout (byte offsets)
     uint32_t o_tab, tab_stride, o_q, o_hist, o_misc, o_cnt, o_seg, o_slots, o_keys, o_union;
     uint32_t sortP;       // power of two >= the CTA's candidate share (fallback sort)
@@ -190,6 +192,23 @@ __device__ __forceinline__ float4 ldg_stream(const float4* p)
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
         : "l"(p));
     return v;
+}
+
+// Per-stage clock stamp of the debug output: thread 0 of each CTA records its
+// SM clock (after the stage's closing barrier) in slot `slot` of the
+// (query, CTA) row; slot 0 holds the SM id, the last two the cycles S4 spent
+// building segment lists and scanning them.
+__device__ __forceinline__ void stamp(const QArgs& A, int64_t b, uint32_t r, int slot)
+{
+    if (A.dbg_clk && threadIdx.x == 0) {
+        long long* row = A.dbg_clk + (b * 16 + r) * NCLK;
+        if (slot == 1) {
+            uint32_t sm;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+            row[0] = (long long)sm;
+        }
+        row[slot] = clock64();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -769,8 +788,12 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
 // (t & 3) of the set, nibble t >> 2, i.e. bits [t & 28, (t & 28) + 4).
 template <int NT>
 __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t m, const uint32_t* sub_pre,
-                              const uint32_t* sub_wb, uint32_t* cnt_words, uint32_t id0, int j0, int j1)
+                              const uint32_t* sub_wb, uint32_t* cnt_words, uint32_t id0, int j0, int j1,
+                              long long* cyc)
 {
+    // cyc (debug, thread 0 only): [0] += cycles listing segments, [1] += cycles
+    // scanning them, accumulated in place so that no value lives across the scan
+    if (cyc) cyc[0] -= clock64();
     // the non-empty segments in flat order, counted in 16-byte quads of the id
     // lists (perm): {quad index of the first quad minus the flat start, perm
     // position of the first id, perm position past the last id, counter word
@@ -832,6 +855,11 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
     }
     if (threadIdx.x == 0) seg_pre[M] = F;
     __syncthreads();
+    if (cyc) {
+        const long long t = clock64();
+        cyc[0] += t;
+        cyc[1] -= t;
+    }
     // each warp takes a contiguous share [wb, we) of the F quads in windows of
     // 32 consecutive quads (one per lane); the warp holds the starts of the
     // next 32 segments in its lanes, so a lane finds the segment of its quad
@@ -901,6 +929,7 @@ __device__ void scan_segments(const QArgs& A, char* smem, uint32_t e0, uint32_t 
         }
     }
     __syncthreads();
+    if (cyc) cyc[1] += clock64();
 }
 
 // Turns the counters of every 32-id group of this CTA into B bit planes in
@@ -1310,6 +1339,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     bool q_next = false;  // the query row is already on its way to o_qn
     while (b < A.nq) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    stamp(A, b, r, 1);
     uint32_t grabbed = 0u;  // thread 0 of CTA 0: the query this cluster answers next
     if (A.work && r == 0 && threadIdx.x == 0) grabbed = Gc + atomicAdd(A.work, 1u);
 
@@ -1357,6 +1387,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         for (int t = threadIdx.x; t < 2 * NC; t += NT) cnt[t] = 0u;
     }
     __syncthreads();
+    stamp(A, b, r, 2);
 
     const uint32_t qT = qpar[0], qC = qpar[1], qk = qpar[2], qper = qpar[3];
     // ---- S1-S3 for the subspaces this CTA owns
@@ -1368,6 +1399,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     } else {
         for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT>(A, smem, b, i, qT, (int)threadIdx.x, 0, 0);
     }
+    stamp(A, b, r, 3);
     // clear the bit planes (the union region served as S3 scratch)
     {
         uint4* pw = reinterpret_cast<uint4*>(smem + A.o_union);
@@ -1376,6 +1408,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         for (uint32_t w = threadIdx.x; w < n16; w += NT) pw[w] = z;
     }
     cluster_sync();  // #1: every subspace's cut and staircase are published
+    stamp(A, b, r, 4);
     // every CTA has read the previous next_q before #1: publish the next query
     if (A.work && r == 0 && threadIdx.x == 0)
         for (int t = 0; t < CL; ++t) st_cluster_u32(map_rank(smem_addr(next_q), (uint32_t)t), grabbed);
@@ -1411,6 +1444,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         sub_pre[A.Ns] = acc;
     }
     __syncthreads();  // sub_pre is read by every thread below
+    stamp(A, b, r, 5);
+    long long* seg_cyc = A.dbg_clk && threadIdx.x == 0 ? A.dbg_clk + (b * 16 + r) * NCLK + NCLK - 2 : nullptr;
+    if (seg_cyc) seg_cyc[0] = seg_cyc[1] = 0;
     uint32_t* planes = reinterpret_cast<uint32_t*>(smem + A.o_union);  // counters, then [B][G] sliced scores
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);  // published: [NC] pass counts, [NC] list counts
     uint32_t* allc = cnt + 2 * NC;                                 // [CL][2][NC]
@@ -1445,7 +1481,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         }
         __syncthreads();
         for (uint32_t e0 = 0; e0 < L; e0 += MAXSEG)
-            scan_segments<NT>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, sub_wb, planes, id0, j0, j1);
+            scan_segments<NT>(A, smem, e0, min((uint32_t)MAXSEG, L - e0), sub_pre, sub_wb, planes, id0, j0, j1,
+                              seg_cyc);
+        stamp(A, b, r, 6);
 
         const uint32_t valid = id0 >= A.n ? 0u : (uint32_t)min((int64_t)A.span, A.n - (int64_t)id0);
         if (!multi) {
@@ -1455,6 +1493,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         }
         counters_to_planes<NT, B>(A, planes, (valid + 31) / 32);
         __syncthreads();
+        stamp(A, b, r, 7);
         if (A.dbg_scores)
             for (uint32_t j = threadIdx.x; j < valid; j += NT) {
                 uint32_t sc = 0;
@@ -1508,7 +1547,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
                 }
             }
         }
+        stamp(A, b, r, 8);
         cluster_sync();  // #2: every CTA's counts are published
+        stamp(A, b, r, 9);
         for (int t = threadIdx.x; t < CL * 2 * NC; t += NT) {
             const int rr = t / (2 * NC), s = t - rr * 2 * NC;
             allc[t] = ld_cluster_u32(map_rank(smem_addr(cnt + s), (uint32_t)rr));
@@ -1585,6 +1626,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             }
         }
         __syncthreads();
+        stamp(A, b, r, 10);
         const uint32_t theta = sel[0], keep = sel[1], need_eq = sel[2];
         if (multi) {
             // this CTA's list entries, in position order: kept ones move to
@@ -1674,9 +1716,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
                 peb += __shfl_sync(0xffffffffu, ie, 31);
             }
         }
+        stamp(A, b, r, 11);
         cluster_sync();  // #3: the new list (or, after one pass, every candidate slot) is filled
+        stamp(A, b, r, 12);
         run_n = keep;
     }
+
     if (A.dbg_cands) {
         const uint32_t mc = qC > r * qper ? min(qper, qC - r * qper) : 0u;
         for (uint32_t t = threadIdx.x; t < mc; t += NT) A.dbg_cands[b * A.C + r * qper + t] = (int32_t)ids_out[t];
@@ -1741,6 +1786,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         __syncthreads();
     }
 
+    stamp(A, b, r, 13);
     // local top-k: a linear bucket histogram of the distances finds a bucket
     // that holds the k-th smallest; only keys up to it are sorted
     uint32_t* khist = reinterpret_cast<uint32_t*>(smem + A.o_union);               // [NB]
@@ -1859,7 +1905,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             st_cluster_u32(rb + 8u * t + 4u, (uint32_t)(v >> 32));
         }
     }
+    stamp(A, b, r, 14);
     cluster_sync();  // #4: every local top-k is in CTA 0; the other CTAs are done
+    stamp(A, b, r, 15);
 
     if (r == 0) {
         // merge by rank: a key's final position is the number of smaller keys
@@ -1897,6 +1945,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             A.out_ids[b * kst + t] = -1;
             A.out_dist[b * kst + t] = __int_as_float(0x7f800000);
         }
+    }
+    if (r == 0) {
+        __syncthreads();
+        stamp(A, b, r, 16);
     }
     // next query: the cluster barriers of its stages order every remote access
     // (next_q was written before #2 and is read after #4)
@@ -2211,6 +2263,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
         A.dbg_scores = dbg->scores;
         A.dbg_cands = dbg->cands;
         A.dbg_surv = dbg->survivors;
+        A.dbg_clk = reinterpret_cast<long long*>(dbg->stage_clock);
     }
     const bool persistent = (p->flags & SUCO_QUERY_ONE_CLUSTER_PER_QUERY) == 0;
     if (p->rank_precision == SUCO_RANK_BF16 || p->rank_precision == SUCO_RANK_FP8) {
@@ -2237,6 +2290,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
             if (base.dbg_scores) C2.dbg_scores = base.dbg_scores + c0 * base.n;
             if (base.dbg_cands) C2.dbg_cands = base.dbg_cands + c0 * (int64_t)base.C;
             if (base.dbg_surv) C2.dbg_surv = base.dbg_surv + c0 * base.n;
+            if (base.dbg_clk) C2.dbg_clk = base.dbg_clk + c0 * 16 * NCLK;
             uint32_t* work = ix->work + (size_t)WORK_STRIDE * (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next,
                                                                                 1u, __ATOMIC_RELAXED) % WORK_SLOTS);
             rc = dispatch(L, NT, nsmax, cnt, persistent, work, st);

@@ -36,7 +36,7 @@ class _QueryParams(C.Structure):
 
 class _DebugOut(C.Structure):
     _fields_ = [("t_eff", C.c_void_p), ("activated", C.c_void_p), ("dtab", C.c_void_p), ("scores", C.c_void_p),
-                ("cands", C.c_void_p), ("survivors", C.c_void_p)]
+                ("cands", C.c_void_p), ("survivors", C.c_void_p), ("stage_clock", C.c_void_p)]
 
 
 class SucoMlp(C.Structure):
@@ -253,13 +253,14 @@ def suco_query_debug(index: SucoIndex, queries: torch.Tensor, k: int, alpha: flo
                dist=torch.empty((nq, k), dtype=torch.float32, device=dev))
     shapes = dict(t_eff=((nq, index.Ns), torch.int64), activated=((nq, index.Ns, index.K), torch.uint8),
                   dtab=((nq, index.Ns, 2, index.sqrtK), torch.float32), scores=((nq, index.n), torch.uint8),
-                  cands=((nq, Cc), torch.int32), survivors=((nq, index.n), torch.uint8))
+                  cands=((nq, Cc), torch.int32), survivors=((nq, index.n), torch.uint8),
+                  stage_clock=((nq, 16, 20), torch.int64))
     for name in want:
         shp, dt = shapes[name]
         fill = 0 if name == "survivors" else (-1 if dt != torch.uint8 else 255)
         out[name] = torch.full(shp, fill, dtype=dt, device=dev)
     dbg = _DebugOut(*[(out[n].data_ptr() if n in out else None) for n in ("t_eff", "activated", "dtab", "scores",
-                                                                        "cands", "survivors")])
+                                                                        "cands", "survivors", "stage_clock")])
     p = _qparams(k, alpha, beta, cluster_size, threads, nq, k_per_query, alpha_per_query, beta_per_query, flags,
                  precision, exact_rerank, id_passes, rank_precision)
     _check(load_library().suco_query_debug(index.handle, _ptr(queries), nq, C.byref(p), _ptr(out["ids"]),

@@ -374,3 +374,30 @@ def test_id_passes_do_not_change_the_answer():
             pkg.suco_query_batch(ix, Qd, 16, 0.1, 0.05, id_passes=128)
     finally:
         pkg.suco_free(ix)
+
+
+@pytest.mark.parametrize("cluster_size,id_passes", [(4, 0), (8, 2)])
+def test_stage_clocks_leave_the_answer_unchanged_and_are_ordered(tiny, cluster_size, id_passes):
+    from paper_2411_14754_gb300 import stage_profile
+    w, X, Q, idx = tiny
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    ix = pkg.suco_build_index_from_assignments(Xd, idx["Ns"], idx["sqrtK"], idx["centroids"], idx["assign"])
+    try:
+        kw = dict(cluster_size=cluster_size, id_passes=id_passes)
+        ids, dist = pkg.suco_query_batch(ix, Qd, w.k, w.alpha, w.beta, **kw)
+        out = pkg.suco_query_debug(ix, Qd, w.k, w.alpha, w.beta, want=("stage_clock",), **kw)
+        torch.cuda.synchronize()
+        assert torch.equal(out["ids"], ids) and torch.equal(out["dist"], dist)
+        clk = out["stage_clock"].cpu().numpy()
+    finally:
+        pkg.suco_free(ix)
+    assert (clk[:, cluster_size:, :] == -1).all()            # rows past the cluster are not written
+    c = clk[:, :cluster_size, :]
+    assert (c[:, :, 0] >= 0).all()                           # SM ids
+    assert (np.diff(c[:, :, 1:16], axis=2) >= 0).all()      # stamps in stage order
+    assert (c[:, 0, 16] >= c[:, 0, 15]).all() and (clk[:, 1:cluster_size, 16] == -1).all()
+    assert (c[:, :, 18] > 0).all() and (c[:, :, 19] > 0).all()
+    res = stage_profile.summarise(clk)
+    assert res["cluster_size"] == cluster_size
+    assert abs(sum(r["share"] for r in res["stages"][:-1]) - 1.0) < 1e-9
