@@ -284,6 +284,38 @@ SUCO_API int suco_adamw_step(float* param, const float* grad, float* m, float* v
                              float beta1, float beta2, float eps, float weight_decay, int32_t step, uint16_t* bf16_copy,
                              void* stream);
 
+/* ---- SC-Linear (Section 3.2, Algorithm 1): the subspace-collision method
+ * without the IMI.  For every query and subspace i, the T = ceil(alpha*n)
+ * points nearest to q in subspace i collide, ordered by (squared subspace
+ * distance, id) with the distance taken in FP32 as acc = fma(x_j - q_j,
+ * x_j - q_j, acc) over the subspace's dims in order; SC-scores (Definition 4);
+ * the C = ceil(beta*n) (at least k) highest scores, ties by lower id, are
+ * re-ranked by exact squared distance and the k nearest returned (ties by id).
+ * It reads the index's copy of D and its subspace layout (Ns), not its IMI.
+ *
+ * suco_sc_linear_workspace_size: bytes of device workspace that a batch of
+ * `batch` queries needs (about Ns*n*4 + n bytes per query, plus 12 bytes per
+ * candidate).  Host only. */
+SUCO_API int suco_sc_linear_workspace_size(const suco_index* index, int64_t batch, int32_t k, double beta,
+                                           size_t* bytes);
+
+/* Answers nq queries by SC-Linear.
+ *   queries    (device) nq x d FP32.   k in [1, 256].   alpha, beta in (0, 1].
+ *   workspace  (device) workspace_bytes of caller-owned scratch; the call
+ *              answers the queries in batches of the largest size whose
+ *              workspace fits (at least one query must fit: SUCO_EINVAL
+ *              otherwise).  Calls that share a workspace must not overlap.
+ *   out_ids, out_dist  (device) nq x k, as suco_query_batch.
+ *   dbg_scores (device, nullable) [nq][n] SC-scores; dbg_cands (device,
+ *              nullable) [nq][C] candidate ids (the ids above the cut score
+ *              first, in id order, then the ties at the cut in id order).
+ * Asynchronous on `stream`; allocates nothing.
+ * Errors: SUCO_EINVAL, SUCO_EUNSUPPORTED (Ns >= 64, or a subspace longer than
+ * 1600 dims), SUCO_ECUDA. */
+SUCO_API int suco_sc_linear(const suco_index* index, const float* queries, int64_t nq, int32_t k, double alpha,
+                            double beta, void* workspace, size_t workspace_bytes, int32_t* out_ids, float* out_dist,
+                            uint8_t* dbg_scores, int32_t* dbg_cands, void* stream);
+
 /* Sizes of an index. */
 typedef struct suco_index_info {
     int64_t n;

@@ -553,10 +553,15 @@ ORC_EXPORT int orc_query_batch_pq(const float* X, int64_t n, int32_t d, int32_t 
 
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1: SC-Linear (no index).  Per subspace, the T points nearest to
- * q in that subspace (sorted by (distance, id)) collide.                     */
+ * q in that subspace (sorted by (distance, id)) collide.  precision 0 takes
+ * the subspace distances in FP64, 1 in the GPU kernel's FP32 arithmetic
+ * (acc = fmaf(x_j - q_j, x_j - q_j, acc) over the subspace's dims in order):
+ * the collisions are a discrete decision that both sides must take in the
+ * same precision.  Optional outputs: scores [n], cands [C].                  */
 
 ORC_EXPORT int orc_sc_linear(const float* X, int64_t n, int32_t d, int32_t Ns, const float* q, int32_t k, int64_t T,
-                             int64_t C, int64_t* out_ids, double* out_dist, int32_t* scores_out)
+                             int64_t C, int32_t precision, int64_t* out_ids, double* out_dist, int32_t* scores_out,
+                             int64_t* cands_out)
 {
     int32_t* scores = (int32_t*)calloc((size_t)n, sizeof(int32_t));
     hit_t* h = (hit_t*)malloc(sizeof(hit_t) * (size_t)n);
@@ -565,7 +570,8 @@ ORC_EXPORT int orc_sc_linear(const float* X, int64_t n, int32_t d, int32_t Ns, c
         orc_subspace_dims(d, Ns, i, &off, &len);
         for (int64_t p = 0; p < n; ++p) {
             h[p].id = p;
-            h[p].dist = sqdist64(X + (size_t)p * d + off, q + off, len);
+            const float* x = X + (size_t)p * d + off;
+            h[p].dist = precision == 1 ? (double)sqdist32(x, q + off, len) : sqdist64(x, q + off, len);
         }
         qsort(h, (size_t)n, sizeof(hit_t), cmp_hit);
         for (int64_t z = 0; z < T; ++z) scores[h[z].id] += 1;
@@ -574,6 +580,7 @@ ORC_EXPORT int orc_sc_linear(const float* X, int64_t n, int32_t d, int32_t Ns, c
     orc_select_candidates(scores, n, C, cands);
     orc_rerank(X, d, q, cands, C, k, out_ids, out_dist);
     if (scores_out) memcpy(scores_out, scores, sizeof(int32_t) * (size_t)n);
+    if (cands_out) memcpy(cands_out, cands, sizeof(int64_t) * (size_t)C);
     free(cands);
     free(h);
     free(scores);

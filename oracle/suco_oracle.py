@@ -62,7 +62,7 @@ def lib():
                                   i32, i32, _i64p, _f64p]
     L.orc_query_batch_pq.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i64, i32, _i64p, _i64p,
                                      i32, i32, _i64p, _f64p]
-    L.orc_sc_linear.argtypes = [_f32p, i64, i32, i32, _f32p, i32, i64, i64, _i64p, _f64p, vp]
+    L.orc_sc_linear.argtypes = [_f32p, i64, i32, i32, _f32p, i32, i64, i64, i32, _i64p, _f64p, vp, vp]
     L.orc_max_threads.restype = C.c_int
     _lib = L
     return L
@@ -275,15 +275,17 @@ def query_batch(X, index, Q, k, T, C_, rank_precision=1, nthreads=1):
     return oi, od
 
 
-def sc_linear(X, Ns, q, k, T, C_):
-    """Algorithm 1 (SC-Linear)."""
+def sc_linear(X, Ns, q, k, T, C_, precision=0, cands=False):
+    """Algorithm 1 (SC-Linear).  precision 0: FP64 subspace distances; 1: the
+    kernel's FP32 arithmetic.  Returns (ids, dist, scores[, cands])."""
     X = _f32(X)
     n, d = X.shape
     oi = np.empty(k, dtype=np.int64)
     od = np.empty(k, dtype=np.float64)
     sc = np.empty(n, dtype=np.int32)
-    lib().orc_sc_linear(X, n, d, Ns, _f32(q), k, int(T), int(C_), oi, od, _ptr(sc))
-    return oi, od, sc
+    cd = np.empty(C_, dtype=np.int64) if cands else None
+    lib().orc_sc_linear(X, n, d, Ns, _f32(q), k, int(T), int(C_), int(precision), oi, od, _ptr(sc), _ptr(cd))
+    return (oi, od, sc, cd) if cands else (oi, od, sc)
 
 
 def max_threads():

@@ -7,4 +7,4 @@ from .suco import (SucoError, SucoIndex, load_library, suco_autotune, suco_build
                    suco_export_index, suco_free, suco_index_get_info, suco_kmeans_noalloc, suco_last_error, suco_query_batch,
                    suco_query_debug, suco_thresholds, suco_version, SucoMlp, suco_query_features,
                    suco_mlp_predict, suco_mlp_forward, suco_mlp_backward, suco_adamw_step, suco_add_reduced_copies, suco_read_status,
-                   suco_inject_fault, FAULT_NONE, FAULT_ALLOC, FAULT_LAUNCH, FAULT_WAIT_TIMEOUT)
+                   suco_inject_fault, suco_sc_linear, suco_sc_linear_workspace_size, FAULT_NONE, FAULT_ALLOC, FAULT_LAUNCH, FAULT_WAIT_TIMEOUT)

@@ -86,6 +86,8 @@ def load_library():
     L.suco_add_reduced_copies.argtypes = [vp, i32, vp]
     L.suco_read_status.argtypes = [vp, C.POINTER(C.c_uint32)]
     L.suco_inject_fault.argtypes = [i32, i32]
+    L.suco_sc_linear_workspace_size.argtypes = [vp, i64, i32, f64, C.POINTER(C.c_size_t)]
+    L.suco_sc_linear.argtypes = [vp, vp, i64, i32, f64, f64, vp, C.c_size_t, vp, vp, vp, vp, vp]
     L.suco_free.argtypes = [vp]
     L.suco_free.restype = None
     L.suco_last_error.restype = C.c_char_p
@@ -93,7 +95,7 @@ def load_library():
                  "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version",
                  "suco_kmeans_noalloc", "suco_autotune", "suco_query_features", "suco_mlp_predict",
                  "suco_mlp_forward", "suco_mlp_backward", "suco_adamw_step", "suco_add_reduced_copies", "suco_read_status",
-                 "suco_inject_fault"):
+                 "suco_inject_fault", "suco_sc_linear_workspace_size", "suco_sc_linear"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -366,6 +368,40 @@ def suco_kmeans_noalloc(data: torch.Tensor, dim_off: int, dim_len: int, centroid
     _check(load_library().suco_kmeans_noalloc(_ptr(data), n, d, dim_off, dim_len, k, iters, _ptr(centroids),
                                               _ptr(assign), _stream(stream)))
     return assign
+
+
+def suco_sc_linear_workspace_size(index: SucoIndex, batch: int, k: int, beta: float) -> int:
+    nb = C.c_size_t()
+    _check(load_library().suco_sc_linear_workspace_size(index.handle, int(batch), int(k), float(beta), C.byref(nb)))
+    return nb.value
+
+
+def suco_sc_linear(index: SucoIndex, queries: torch.Tensor, k: int, alpha: float, beta: float,
+                   workspace: Optional[torch.Tensor] = None, batch: int = 32, out_ids=None, out_dist=None,
+                   debug: bool = False, stream=None):
+    """SC-Linear (Algorithm 1) for every row of ``queries``.  ``workspace``: a
+    uint8 CUDA tensor (allocated for ``batch`` queries when not given).
+    Returns (ids, dists) or, with debug, (ids, dists, scores [nq][n] uint8,
+    cands [nq][C] int32)."""
+    _dev_f32(queries, "queries")
+    nq = queries.shape[0]
+    dev = queries.device
+    if workspace is None:
+        nb = suco_sc_linear_workspace_size(index, max(1, min(batch, nq)), k, beta)
+        workspace = torch.empty(nb, dtype=torch.uint8, device=dev)
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    sc = cd = None
+    if debug:
+        _, Cc = suco_thresholds(index.n, alpha, beta, k)
+        sc = torch.full((nq, index.n), 255, dtype=torch.uint8, device=dev)
+        cd = torch.full((nq, Cc), -1, dtype=torch.int32, device=dev)
+    _check(load_library().suco_sc_linear(index.handle, _ptr(queries), nq, int(k), float(alpha), float(beta),
+                                         _ptr(workspace), workspace.numel(), _ptr(out_ids), _ptr(out_dist), _ptr(sc),
+                                         _ptr(cd), _stream(stream)))
+    return (out_ids, out_dist, sc, cd) if debug else (out_ids, out_dist)
 
 
 def suco_free(index: SucoIndex):

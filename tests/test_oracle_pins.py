@@ -446,3 +446,56 @@ def test_query_from_tables_written_from_the_definition_equals_the_fp64_query():
         # a transposed table (halves swapped) must change the ranking somewhere
         sw = oracle.query_from_tables(X, idx, qq, 8, T=120, C_=35, dtab=tab[:, ::-1, :].copy())
         assert not np.array_equal(sw["activated"], o["activated"])
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (SC-Linear)
+
+def _sc_linear_brute(X, Ns, q, T, C):
+    """Algorithm 1 written with library routines: per subspace the first T ids
+    of a lexsort by (squared distance, id) collide; candidates are the first C
+    ids by (score desc, id asc)."""
+    n, d = X.shape
+    s = d // Ns
+    scores = np.zeros(n, np.int64)
+    for i in range(Ns):
+        off, ln = i * s, (d - (Ns - 1) * s if i == Ns - 1 else s)
+        dist = cdist(q[None, off:off + ln].astype(np.float64), X[:, off:off + ln].astype(np.float64),
+                     "sqeuclidean")[0]
+        scores[np.lexsort((np.arange(n), dist))[:T]] += 1
+    return scores, np.lexsort((np.arange(n), -scores))[:C]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sc_linear_against_brute_force(precision):
+    X = W.dataset(1, n=2500)
+    for qq in W.queries(1, nq=3):
+        ids, dist, sc, cands = oracle.sc_linear(X, 8, qq, 10, 125, 40, precision=precision, cands=True)
+        bs, bc = _sc_linear_brute(X, 8, qq, 125, 40)
+        np.testing.assert_array_equal(sc, bs)
+        assert sorted(cands.tolist()) == sorted(bc.tolist())
+        ri, rd = oracle.rerank(X, qq, bc, 10)
+        assert ids.tolist() == ri.tolist()
+
+
+def test_sc_linear_fp32_equals_fp64_on_exact_data_and_handles_ties():
+    # small integers: every subspace distance is an exact integer in both
+    # precisions; many equal distances test the (distance, id) order
+    X = W.random_data(71, 3000, 12, kind="int")
+    for qq in W.random_data(72, 4, 12, kind="int"):
+        a = oracle.sc_linear(X, 3, qq, 7, 300, 50, precision=0, cands=True)
+        b = oracle.sc_linear(X, 3, qq, 7, 300, 50, precision=1, cands=True)
+        bs, bc = _sc_linear_brute(X, 3, qq, 300, 50)
+        for r in (a, b):
+            np.testing.assert_array_equal(r[2], bs)
+            np.testing.assert_array_equal(np.sort(r[3]), np.sort(bc))
+
+
+def test_sc_linear_alpha_one_and_alpha_beta_one():
+    X = W.dataset(1, n=800)
+    qq = W.queries(1, nq=1)[0]
+    ids, dist, sc = oracle.sc_linear(X, 4, qq, 9, 800, 30, precision=1)
+    assert (sc == 4).all()
+    ids, dist, sc = oracle.sc_linear(X, 4, qq, 9, 800, 800, precision=1)
+    ei, ed = exact_knn(X, qq, 9)
+    assert ids.tolist() == ei.tolist()
