@@ -65,6 +65,7 @@ def parse():
                    help="cheapest margin pairs (by modelled bytes) timed for the learned arm")
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
                    help="re-rank precision of the fixed-ratio path")
+    p.add_argument("--sc-linear", action="store_true", help="time SC-Linear (Algorithm 1, no index) instead")
     p.add_argument("--rank-precision", default="fp32", choices=["fp32", "bf16", "fp8"],
                    help="centroid-distance arithmetic of the fixed-ratio path (bf16: tensor cores)")
     return p.parse_args()
@@ -736,6 +737,62 @@ def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     pkg.suco_free(index)
 
 
+def run_sc_linear(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
+    """SC-Linear (Algorithm 1): every point's distance to the query in every
+    subspace, the exact alpha*n nearest per subspace, SC-scores, the beta*n
+    best candidates, exact re-rank.  A step is one batch of queries."""
+    w = W.WORKLOADS[args.workload]
+    X = W.dataset(w.number)
+    Xd = torch.from_numpy(X).to(dev)
+    index = pkg.suco_build_index(Xd, w.Ns, 2, 0, seed=1)   # SC-Linear reads the dataset copy and the layout only
+    del Xd
+    B = 64
+    Qall = W.queries(w.number, nq=max(B * 4, 256))
+    nb = len(Qall) // B
+    batches = [torch.from_numpy(Qall[i * B:(i + 1) * B]).to(dev) for i in range(nb)]
+    order = replicas.batch_order(rank, world, nb)
+    ws = torch.empty(pkg.suco_sc_linear_workspace_size(index, B, w.k, w.beta), dtype=torch.uint8, device=dev)
+    outs = [(torch.empty((B, w.k), dtype=torch.int32, device=dev), torch.empty((B, w.k), dtype=torch.float32,
+                                                                               device=dev)) for _ in batches]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s, ev):
+        bi = order[s % nb]
+        pkg.suco_sc_linear(index, batches[bi], w.k, w.alpha, w.beta, workspace=ws, out_ids=outs[bi][0],
+                           out_dist=outs[bi][1], stream=stream)
+
+    if world > 1:
+        tdist.barrier()
+    with ClockSampler(local_rank) as clk:
+        total_ms, _ = time_loop(torch, stream, args.steps, args.warmup, step, label="timed")
+    total_ms, all_q = replicas.reduce_throughput(tdist, dev, total_ms, float(B * args.steps), world)
+    value = all_q / (total_ms / 1000.0)
+    from paper_2411_14754_gb300 import learn as L
+    Xg = torch.from_numpy(X).to(dev)
+    gt = L.exact_knn(Xg, batches[0], w.k)
+    del Xg
+    rec = float(L.recall_rows(outs[0][0].cpu().numpy(), gt).mean())
+    # the distance pass dominates: per point, query and dimension one FP32
+    # subtract and one fused multiply-add; peak = 152 SMs x 128 FP32 lanes x clock
+    peak = 152 * 128 * 2.07e9 / 1e12
+    achieved = 2.0 * w.n * w.d * B / (total_ms / args.steps / 1000.0) / 1e12
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(w, B),
+                "method": {"arm": f"SC-Linear (Algorithm 1, no index), alpha={w.alpha}, beta={w.beta}"},
+                "recall_at_k": rec, "recall_sample": B, "k": w.k,
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 instr/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                             "kernel": "whole SC-Linear path per step (the distance pass dominates)"},
+                "clocks": clk.summary(), "gpu_launches": 9 * args.steps, "cpu_baseline": None,
+                "e2e": None}
+        print(json.dumps(line), flush=True)
+    pkg.suco_free(index)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -754,6 +811,11 @@ def main():
     dev = torch.device("cuda", local_rank)
     pkg.load_library()
     w = W.WORKLOADS[args.workload]
+    if args.sc_linear:
+        run_sc_linear(args, torch, tdist, pkg, W, rank, local_rank, world, dev)
+        if world > 1:
+            tdist.destroy_process_group()
+        return
     if w.k_mix and not args.plain:
         run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev)
         if world > 1:

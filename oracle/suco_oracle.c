@@ -116,24 +116,29 @@ ORC_EXPORT int64_t orc_candidate_count(double beta, int64_t n, int32_t k)
 /* ------------------------------------------------------------------------ */
 /* Distances                                                                 */
 
-/* Squared Euclidean distance between two vectors of length len, FP64. */
-static double sqdist64(const float* a, const float* b, int32_t len)
+/* The distance between two vectors of length len, FP64.  metric 0: squared
+ * Euclidean (the paper's default); metric 1: Manhattan (L1), the variant of
+ * Section 5's distance-measure experiment (SuCo-L1).  Both are sums of
+ * per-dimension terms, so a cell's value d1 + d2 is the distance to its
+ * product centroid in either metric. */
+static double dist64(const float* a, const float* b, int32_t len, int32_t metric)
 {
     double acc = 0.0;
     for (int32_t j = 0; j < len; ++j) {
         double t = (double)a[j] - (double)b[j];
-        acc += t * t;
+        acc += metric == 1 ? fabs(t) : t * t;
     }
     return acc;
 }
 
-/* Same, FP32 with one fused multiply-add per dimension in ascending order. */
-static float sqdist32(const float* a, const float* b, int32_t len)
+/* Same, FP32 in ascending dimension order: acc = fmaf(t, t, acc) for the
+ * squared Euclidean distance, acc = acc + |t| for L1 (t = a_j - b_j). */
+static float dist32(const float* a, const float* b, int32_t len, int32_t metric)
 {
     float acc = 0.0f;
     for (int32_t j = 0; j < len; ++j) {
         float t = a[j] - b[j];
-        acc = fmaf(t, t, acc);
+        acc = metric == 1 ? acc + fabsf(t) : fmaf(t, t, acc);
     }
     return acc;
 }
@@ -275,12 +280,12 @@ ORC_EXPORT void orc_select_candidates(const int32_t* scores, int64_t n, int64_t 
 /* Exact squared distances from q to the listed rows, sorted by (dist, id);
  * the first k go out, padded with (-1, +inf). */
 ORC_EXPORT void orc_rerank(const float* X, int32_t d, const float* q, const int64_t* ids, int64_t m, int32_t k,
-                           int64_t* out_ids, double* out_dist)
+                           int64_t* out_ids, double* out_dist, int32_t metric)
 {
     hit_t* h = (hit_t*)malloc(sizeof(hit_t) * (size_t)(m > 0 ? m : 1));
     for (int64_t z = 0; z < m; ++z) {
         h[z].id = ids[z];
-        h[z].dist = sqdist64(X + (size_t)ids[z] * (size_t)d, q, d);
+        h[z].dist = dist64(X + (size_t)ids[z] * (size_t)d, q, d, metric);
     }
     qsort(h, (size_t)m, sizeof(hit_t), cmp_hit);
     for (int32_t z = 0; z < k; ++z) {
@@ -297,11 +302,11 @@ ORC_EXPORT void orc_rerank(const float* X, int32_t d, const float* q, const int6
 
 /* Exact k-NN over the whole dataset (the recall reference of Section 5.1). */
 ORC_EXPORT void orc_bruteforce_knn(const float* X, int64_t n, int32_t d, const float* q, int32_t k,
-                                   int64_t* out_ids, double* out_dist)
+                                   int64_t* out_ids, double* out_dist, int32_t metric)
 {
     int64_t* all = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
     for (int64_t i = 0; i < n; ++i) all[i] = i;
-    orc_rerank(X, d, q, all, n, k, out_ids, out_dist);
+    orc_rerank(X, d, q, all, n, k, out_ids, out_dist, metric);
     free(all);
 }
 
@@ -312,7 +317,7 @@ ORC_EXPORT void orc_bruteforce_knn(const float* X, int64_t n, int32_t d, const f
  * cent: k*len doubles out.  assign: n ints out (assignment from the last
  * assignment step, i.e. against the centroids before the last update).     */
 ORC_EXPORT void orc_kmeans(const float* X, int64_t n, int32_t d, int32_t off, int32_t len, int32_t k,
-                           int32_t iters, const int64_t* init_ids, double* cent, int32_t* assign)
+                           int32_t iters, const int64_t* init_ids, double* cent, int32_t* assign, int32_t metric)
 {
     for (int32_t a = 0; a < k; ++a)
         for (int32_t j = 0; j < len; ++j) cent[(size_t)a * len + j] = (double)X[(size_t)init_ids[a] * d + off + j];
@@ -328,7 +333,7 @@ ORC_EXPORT void orc_kmeans(const float* X, int64_t n, int32_t d, int32_t off, in
                 double acc = 0.0;
                 for (int32_t j = 0; j < len; ++j) {
                     double t = (double)x[j] - cent[(size_t)a * len + j];
-                    acc += t * t;
+                    acc += metric == 1 ? fabs(t) : t * t;
                 }
                 if (acc < bd) {
                     bd = acc;
@@ -356,13 +361,13 @@ ORC_EXPORT void orc_kmeans(const float* X, int64_t n, int32_t d, int32_t off, in
 
 /* Nearest stored (FP32) centroid of each point, FP64 distances, ties low. */
 ORC_EXPORT void orc_assign_nearest(const float* X, int64_t n, int32_t d, int32_t off, int32_t len, const float* cent,
-                                   int32_t k, int32_t cent_stride, int32_t* assign)
+                                   int32_t k, int32_t cent_stride, int32_t* assign, int32_t metric)
 {
     for (int64_t p = 0; p < n; ++p) {
         int32_t best = 0;
         double bd = INFINITY;
         for (int32_t a = 0; a < k; ++a) {
-            double acc = sqdist64(X + (size_t)p * d + off, cent + (size_t)a * cent_stride, len);
+            double acc = dist64(X + (size_t)p * d + off, cent + (size_t)a * cent_stride, len, metric);
             if (acc < bd) {
                 bd = acc;
                 best = a;
@@ -395,7 +400,7 @@ ORC_EXPORT void orc_imi_from_assign(const int32_t* assign1, const int32_t* assig
  * init_ids: [Ns][2][sqrtK] point ids that seed Lloyd's iterations. */
 ORC_EXPORT void orc_build_index(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, int32_t iters,
                                 const int64_t* init_ids, float* centroids, int32_t* assign, int64_t* cell_off,
-                                int64_t* perm, int32_t nthreads)
+                                int64_t* perm, int32_t nthreads, int32_t metric)
 {
     int32_t hmax = orc_hmax(d, Ns);
     int64_t K = (int64_t)sqrtK * sqrtK;
@@ -409,11 +414,11 @@ ORC_EXPORT void orc_build_index(const float* X, int64_t n, int32_t d, int32_t Ns
         orc_half_dims(d, Ns, i, h, &off, &len);
         double* cent = (double*)malloc(sizeof(double) * (size_t)sqrtK * len);
         int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-        orc_kmeans(X, n, d, off, len, sqrtK, iters, init_ids + (size_t)ih * sqrtK, cent, tmp);
+        orc_kmeans(X, n, d, off, len, sqrtK, iters, init_ids + (size_t)ih * sqrtK, cent, tmp, metric);
         float* cf = centroids + (size_t)ih * sqrtK * hmax;
         for (int32_t a = 0; a < sqrtK; ++a)
             for (int32_t j = 0; j < len; ++j) cf[(size_t)a * hmax + j] = (float)cent[(size_t)a * len + j];
-        orc_assign_nearest(X, n, d, off, len, cf, sqrtK, hmax, assign + (size_t)ih * n);
+        orc_assign_nearest(X, n, d, off, len, cf, sqrtK, hmax, assign + (size_t)ih * n, metric);
         free(cent);
         free(tmp);
     }
@@ -437,7 +442,7 @@ static int query_core(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t 
                       const int64_t* cell_off, const int64_t* perm, const float* q, int32_t k, int64_t T, int64_t C,
                       int32_t rank_precision, const double* dtab_in, int64_t* out_ids, double* out_dist,
                       int32_t* scores_out, int64_t* cands_out, int64_t* teff_out, uint8_t* activated_out,
-                      double* dtab_out)
+                      double* dtab_out, int32_t metric)
 {
     int32_t hmax = orc_hmax(d, Ns);
     int64_t K = (int64_t)sqrtK * sqrtK;
@@ -459,9 +464,9 @@ static int query_core(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t 
                 if (dtab_in)
                     dd[a] = dtab_in[((size_t)i * 2 + h) * sqrtK + a];
                 else if (rank_precision == 1)
-                    dd[a] = (double)sqdist32(q + off, cb + (size_t)a * hmax, len);
+                    dd[a] = (double)dist32(q + off, cb + (size_t)a * hmax, len, metric);
                 else
-                    dd[a] = sqdist64(q + off, cb + (size_t)a * hmax, len);
+                    dd[a] = dist64(q + off, cb + (size_t)a * hmax, len, metric);
             }
             if (dtab_out)
                 for (int32_t a = 0; a < sqrtK; ++a) dtab_out[((size_t)i * 2 + h) * sqrtK + a] = dd[a];
@@ -484,7 +489,7 @@ static int query_core(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t 
     }
     int64_t* cands = (int64_t*)malloc(sizeof(int64_t) * (size_t)C);
     orc_select_candidates(scores, n, C, cands);
-    orc_rerank(X, d, q, cands, C, k, out_ids, out_dist);
+    orc_rerank(X, d, q, cands, C, k, out_ids, out_dist, metric);
     if (scores_out) memcpy(scores_out, scores, sizeof(int32_t) * (size_t)n);
     if (cands_out) memcpy(cands_out, cands, sizeof(int64_t) * (size_t)C);
     free(cands);
@@ -501,10 +506,11 @@ static int query_core(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t 
 ORC_EXPORT int orc_query(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, const float* centroids,
                          const int64_t* cell_off, const int64_t* perm, const float* q, int32_t k, int64_t T,
                          int64_t C, int32_t rank_precision, int64_t* out_ids, double* out_dist, int32_t* scores_out,
-                         int64_t* cands_out, int64_t* teff_out, uint8_t* activated_out, double* dtab_out)
+                         int64_t* cands_out, int64_t* teff_out, uint8_t* activated_out, double* dtab_out,
+                         int32_t metric)
 {
     return query_core(X, n, d, Ns, sqrtK, centroids, cell_off, perm, q, k, T, C, rank_precision, NULL, out_ids,
-                      out_dist, scores_out, cands_out, teff_out, activated_out, dtab_out);
+                      out_dist, scores_out, cands_out, teff_out, activated_out, dtab_out, metric);
 }
 
 /* Algorithm 4 for one query from given centroid-distance tables (the ranking
@@ -513,17 +519,17 @@ ORC_EXPORT int orc_query_from_tables(const float* X, int64_t n, int32_t d, int32
                                      const float* centroids, const int64_t* cell_off, const int64_t* perm,
                                      const float* q, int32_t k, int64_t T, int64_t C, const double* dtab_in,
                                      int64_t* out_ids, double* out_dist, int32_t* scores_out, int64_t* cands_out,
-                                     int64_t* teff_out, uint8_t* activated_out)
+                                     int64_t* teff_out, uint8_t* activated_out, int32_t metric)
 {
     return query_core(X, n, d, Ns, sqrtK, centroids, cell_off, perm, q, k, T, C, 1, dtab_in, out_ids, out_dist,
-                      scores_out, cands_out, teff_out, activated_out, NULL);
+                      scores_out, cands_out, teff_out, activated_out, NULL, metric);
 }
 
 /* Algorithm 4 over a batch of nq queries, one query per OpenMP thread. */
 ORC_EXPORT int orc_query_batch(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, const float* centroids,
                                const int64_t* cell_off, const int64_t* perm, const float* Q, int64_t nq, int32_t k,
                                int64_t T, int64_t C, int32_t rank_precision, int32_t nthreads, int64_t* out_ids,
-                               double* out_dist)
+                               double* out_dist, int32_t metric)
 {
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
@@ -531,7 +537,7 @@ ORC_EXPORT int orc_query_batch(const float* X, int64_t n, int32_t d, int32_t Ns,
 #endif
     for (int64_t b = 0; b < nq; ++b)
         orc_query(X, n, d, Ns, sqrtK, centroids, cell_off, perm, Q + (size_t)b * d, k, T, C, rank_precision,
-                  out_ids + (size_t)b * k, out_dist + (size_t)b * k, NULL, NULL, NULL, NULL, NULL);
+                  out_ids + (size_t)b * k, out_dist + (size_t)b * k, NULL, NULL, NULL, NULL, NULL, metric);
     return 0;
 }
 
@@ -539,7 +545,7 @@ ORC_EXPORT int orc_query_batch(const float* X, int64_t n, int32_t d, int32_t Ns,
 ORC_EXPORT int orc_query_batch_pq(const float* X, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
                                   const float* centroids, const int64_t* cell_off, const int64_t* perm, const float* Q,
                                   int64_t nq, int32_t k, const int64_t* T, const int64_t* C, int32_t rank_precision,
-                                  int32_t nthreads, int64_t* out_ids, double* out_dist)
+                                  int32_t nthreads, int64_t* out_ids, double* out_dist, int32_t metric)
 {
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
@@ -547,7 +553,7 @@ ORC_EXPORT int orc_query_batch_pq(const float* X, int64_t n, int32_t d, int32_t 
 #endif
     for (int64_t b = 0; b < nq; ++b)
         orc_query(X, n, d, Ns, sqrtK, centroids, cell_off, perm, Q + (size_t)b * d, k, T[b], C[b], rank_precision,
-                  out_ids + (size_t)b * k, out_dist + (size_t)b * k, NULL, NULL, NULL, NULL, NULL);
+                  out_ids + (size_t)b * k, out_dist + (size_t)b * k, NULL, NULL, NULL, NULL, NULL, metric);
     return 0;
 }
 
@@ -561,7 +567,7 @@ ORC_EXPORT int orc_query_batch_pq(const float* X, int64_t n, int32_t d, int32_t 
 
 ORC_EXPORT int orc_sc_linear(const float* X, int64_t n, int32_t d, int32_t Ns, const float* q, int32_t k, int64_t T,
                              int64_t C, int32_t precision, int64_t* out_ids, double* out_dist, int32_t* scores_out,
-                             int64_t* cands_out)
+                             int64_t* cands_out, int32_t metric)
 {
     int32_t* scores = (int32_t*)calloc((size_t)n, sizeof(int32_t));
     hit_t* h = (hit_t*)malloc(sizeof(hit_t) * (size_t)n);
@@ -571,14 +577,14 @@ ORC_EXPORT int orc_sc_linear(const float* X, int64_t n, int32_t d, int32_t Ns, c
         for (int64_t p = 0; p < n; ++p) {
             h[p].id = p;
             const float* x = X + (size_t)p * d + off;
-            h[p].dist = precision == 1 ? (double)sqdist32(x, q + off, len) : sqdist64(x, q + off, len);
+            h[p].dist = precision == 1 ? (double)dist32(x, q + off, len, metric) : dist64(x, q + off, len, metric);
         }
         qsort(h, (size_t)n, sizeof(hit_t), cmp_hit);
         for (int64_t z = 0; z < T; ++z) scores[h[z].id] += 1;
     }
     int64_t* cands = (int64_t*)malloc(sizeof(int64_t) * (size_t)C);
     orc_select_candidates(scores, n, C, cands);
-    orc_rerank(X, d, q, cands, C, k, out_ids, out_dist);
+    orc_rerank(X, d, q, cands, C, k, out_ids, out_dist, metric);
     if (scores_out) memcpy(scores_out, scores, sizeof(int32_t) * (size_t)n);
     if (cands_out) memcpy(cands_out, cands, sizeof(int64_t) * (size_t)C);
     free(cands);

@@ -46,23 +46,23 @@ def lib():
                                          C.POINTER(i64), vp]
     L.orc_dynamic_activation.restype = i64
     L.orc_select_candidates.argtypes = [_i32p, i64, i64, _i64p]
-    L.orc_rerank.argtypes = [_f32p, i32, _f32p, _i64p, i64, i32, _i64p, _f64p]
-    L.orc_bruteforce_knn.argtypes = [_f32p, i64, i32, _f32p, i32, _i64p, _f64p]
-    L.orc_kmeans.argtypes = [_f32p, i64, i32, i32, i32, i32, i32, _i64p, _f64p, _i32p]
-    L.orc_assign_nearest.argtypes = [_f32p, i64, i32, i32, i32, _f32p, i32, i32, _i32p]
+    L.orc_rerank.argtypes = [_f32p, i32, _f32p, _i64p, i64, i32, _i64p, _f64p, i32]
+    L.orc_bruteforce_knn.argtypes = [_f32p, i64, i32, _f32p, i32, _i64p, _f64p, i32]
+    L.orc_kmeans.argtypes = [_f32p, i64, i32, i32, i32, i32, i32, _i64p, _f64p, _i32p, i32]
+    L.orc_assign_nearest.argtypes = [_f32p, i64, i32, i32, i32, _f32p, i32, i32, _i32p, i32]
     L.orc_imi_from_assign.argtypes = [_i32p, _i32p, i64, i32, _i64p, _i64p]
-    L.orc_build_index.argtypes = [_f32p, i64, i32, i32, i32, i32, _i64p, _f32p, _i32p, _i64p, _i64p, i32]
+    L.orc_build_index.argtypes = [_f32p, i64, i32, i32, i32, i32, _i64p, _f32p, _i32p, _i64p, _i64p, i32, i32]
     L.orc_query.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i32, i64, i64, i32,
-                            _i64p, _f64p, vp, vp, vp, vp, vp]
+                            _i64p, _f64p, vp, vp, vp, vp, vp, i32]
     L.orc_query.restype = C.c_int
     L.orc_query_from_tables.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i32, i64, i64, _f64p,
-                                        _i64p, _f64p, vp, vp, vp, vp]
+                                        _i64p, _f64p, vp, vp, vp, vp, i32]
     L.orc_query_from_tables.restype = C.c_int
     L.orc_query_batch.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i64, i32, i64, i64,
-                                  i32, i32, _i64p, _f64p]
+                                  i32, i32, _i64p, _f64p, i32]
     L.orc_query_batch_pq.argtypes = [_f32p, i64, i32, i32, i32, _f32p, _i64p, _i64p, _f32p, i64, i32, _i64p, _i64p,
-                                     i32, i32, _i64p, _f64p]
-    L.orc_sc_linear.argtypes = [_f32p, i64, i32, i32, _f32p, i32, i64, i64, i32, _i64p, _f64p, vp, vp]
+                                     i32, i32, _i64p, _f64p, i32]
+    L.orc_sc_linear.argtypes = [_f32p, i64, i32, i32, _f32p, i32, i64, i64, i32, _i64p, _f64p, vp, vp, i32]
     L.orc_max_threads.restype = C.c_int
     _lib = L
     return L
@@ -78,6 +78,36 @@ def _f32(a):
 
 # --------------------------------------------------------------------------
 # Layout and thresholds (Definition 3; Algorithm 2; reading R4)
+
+METRIC_L2, METRIC_L1 = 0, 1
+
+
+def sampled_subspaces(dim_perm, Ns):
+    """Definition 3's subspaces from a sampling given as a permutation of the
+    d dims: round i < Ns-1 takes the floor(d/Ns) dims dim_perm[i*s:(i+1)*s]
+    (sampled without replacement: each dim at most once), the last subspace
+    every remaining dim.  Returns the list of Ns dim lists."""
+    perm = np.asarray(dim_perm, dtype=np.int64)
+    d = len(perm)
+    assert sorted(perm.tolist()) == list(range(d)), "not a permutation of the dims"
+    s = d // Ns
+    return [perm[i * s:(i + 1) * s] if i < Ns - 1 else perm[(Ns - 1) * s:] for i in range(Ns)]
+
+
+def _columns(X, index):
+    """The dataset's columns in the index's sampling order (subspace i then
+    occupies the contiguous block that Definition 3's contiguous case gives it)."""
+    if index is None or index.get("dim_perm") is None:
+        return _f32(X)
+    if "Xp" in index and index["Xp"].shape == X.shape:
+        return index["Xp"]
+    return np.ascontiguousarray(np.asarray(X, dtype=np.float32)[:, index["dim_perm"]])
+
+
+def _query_cols(q, index):
+    if index is None or index.get("dim_perm") is None:
+        return _f32(q)
+    return np.ascontiguousarray(np.asarray(q, dtype=np.float32)[..., index["dim_perm"]])
 
 def subspace_dims(d, Ns, i):
     off, ln = C.c_int32(), C.c_int32()
@@ -137,40 +167,42 @@ def select_candidates(scores, C_):
     return out
 
 
-def rerank(X, q, ids, k):
+def rerank(X, q, ids, k, metric=METRIC_L2):
     X = _f32(X)
     ids = np.ascontiguousarray(ids, dtype=np.int64)
     oi = np.empty(k, dtype=np.int64)
     od = np.empty(k, dtype=np.float64)
-    lib().orc_rerank(X, X.shape[1], _f32(q), ids, len(ids), k, oi, od)
+    lib().orc_rerank(X, X.shape[1], _f32(q), ids, len(ids), k, oi, od, int(metric))
     return oi, od
 
 
-def bruteforce_knn(X, q, k):
+def bruteforce_knn(X, q, k, metric=METRIC_L2):
     X = _f32(X)
     oi = np.empty(k, dtype=np.int64)
     od = np.empty(k, dtype=np.float64)
-    lib().orc_bruteforce_knn(X, X.shape[0], X.shape[1], _f32(q), k, oi, od)
+    lib().orc_bruteforce_knn(X, X.shape[0], X.shape[1], _f32(q), k, oi, od, int(metric))
     return oi, od
 
 
 # --------------------------------------------------------------------------
 # Algorithm 2
 
-def kmeans(X, off, ln, k, iters, init_ids):
+def kmeans(X, off, ln, k, iters, init_ids, metric=METRIC_L2):
+    """Lloyd's iterations: nearest centroid under the metric, then member means."""
     X = _f32(X)
     cent = np.empty((k, ln), dtype=np.float64)
     assign = np.empty(X.shape[0], dtype=np.int32)
     lib().orc_kmeans(X, X.shape[0], X.shape[1], off, ln, k, iters,
-                     np.ascontiguousarray(init_ids, dtype=np.int64), cent, assign)
+                     np.ascontiguousarray(init_ids, dtype=np.int64), cent, assign, int(metric))
     return cent, assign
 
 
-def assign_nearest(X, off, ln, cent_f32):
+def assign_nearest(X, off, ln, cent_f32, metric=METRIC_L2):
     X = _f32(X)
     cent = _f32(cent_f32)
     out = np.empty(X.shape[0], dtype=np.int32)
-    lib().orc_assign_nearest(X, X.shape[0], X.shape[1], off, ln, cent, cent.shape[0], cent.shape[1], out)
+    lib().orc_assign_nearest(X, X.shape[0], X.shape[1], off, ln, cent, cent.shape[0], cent.shape[1], out,
+                             int(metric))
     return out
 
 
@@ -184,9 +216,18 @@ def imi_from_assign(a1, a2, sqrtK):
     return off, perm
 
 
-def build_index(X, Ns, sqrtK, iters, init_ids, nthreads=None):
+def build_index(X, Ns, sqrtK, iters, init_ids, nthreads=None, metric=METRIC_L2, dim_perm=None):
     """Algorithm 2.  Returns a dict with centroids [Ns,2,sqrtK,hmax] (FP32),
-    assign [Ns,2,n], cell_off [Ns,K+1], perm [Ns,n]."""
+    assign [Ns,2,n], cell_off [Ns,K+1], perm [Ns,n].  metric: the distance of
+    the nearest-centroid assignments; dim_perm: Definition 3's subspace
+    sampling (see sampled_subspaces), None for contiguous subspaces.  The
+    centroids of subspace i are over its dims in the sampling's order."""
+    if dim_perm is not None:
+        sampled_subspaces(dim_perm, Ns)
+        Xp = np.ascontiguousarray(np.asarray(X, dtype=np.float32)[:, np.asarray(dim_perm, dtype=np.int64)])
+        idx = build_index(Xp, Ns, sqrtK, iters, init_ids, nthreads, metric)
+        idx.update(dim_perm=np.asarray(dim_perm, dtype=np.int64), Xp=Xp)
+        return idx
     X = _f32(X)
     n, d = X.shape
     hm = hmax(d, Ns)
@@ -197,11 +238,11 @@ def build_index(X, Ns, sqrtK, iters, init_ids, nthreads=None):
     off = np.empty((Ns, K + 1), dtype=np.int64)
     perm = np.empty((Ns, n), dtype=np.int64)
     nt = nthreads if nthreads else max(1, min(2 * Ns, os.cpu_count() or 1))
-    lib().orc_build_index(X, n, d, Ns, sqrtK, iters, init, cent, assign, off, perm, nt)
-    return dict(Ns=Ns, sqrtK=sqrtK, centroids=cent, assign=assign, cell_off=off, perm=perm)
+    lib().orc_build_index(X, n, d, Ns, sqrtK, iters, init, cent, assign, off, perm, nt, int(metric))
+    return dict(Ns=Ns, sqrtK=sqrtK, centroids=cent, assign=assign, cell_off=off, perm=perm, metric=int(metric))
 
 
-def index_from_parts(Ns, sqrtK, centroids, assign):
+def index_from_parts(Ns, sqrtK, centroids, assign, metric=METRIC_L2):
     """The IMI (R8) of a given set of FP32 centroids and assignments."""
     assign = np.ascontiguousarray(assign, dtype=np.int32)
     n = assign.shape[2]
@@ -210,7 +251,8 @@ def index_from_parts(Ns, sqrtK, centroids, assign):
     perm = np.empty((Ns, n), dtype=np.int64)
     for i in range(Ns):
         off[i], perm[i] = imi_from_assign(assign[i, 0], assign[i, 1], sqrtK)
-    return dict(Ns=Ns, sqrtK=sqrtK, centroids=_f32(centroids), assign=assign, cell_off=off, perm=perm)
+    return dict(Ns=Ns, sqrtK=sqrtK, centroids=_f32(centroids), assign=assign, cell_off=off, perm=perm,
+                metric=int(metric))
 
 
 # --------------------------------------------------------------------------
@@ -218,8 +260,11 @@ def index_from_parts(Ns, sqrtK, centroids, assign):
 
 def query(X, index, q, k, T, C_, rank_precision=1, debug=True):
     """Algorithm 4 for one query.  rank_precision 1 takes the cell-ranking
-    decisions in the GPU kernel's FP32 arithmetic, 0 in FP64."""
-    X = _f32(X)
+    decisions in the GPU kernel's FP32 arithmetic, 0 in FP64.  The index's
+    metric and subspace sampling apply (distances are then L1 for METRIC_L1;
+    results are ids of X and their distances)."""
+    X = _columns(X, index)
+    q = _query_cols(q, index)
     n, d = X.shape
     Ns, sk = index["Ns"], index["sqrtK"]
     K = sk * sk
@@ -233,14 +278,15 @@ def query(X, index, q, k, T, C_, rank_precision=1, debug=True):
     lib().orc_query(X, n, d, Ns, sk, index["centroids"], index["cell_off"], index["perm"], _f32(q), k, int(T),
                     int(C_), rank_precision, oi, od,
                     _ptr(out.get("scores")), _ptr(out.get("cands")), _ptr(out.get("teff")),
-                    _ptr(out.get("activated")), _ptr(out.get("dtab")))
+                    _ptr(out.get("activated")), _ptr(out.get("dtab")), int(index.get("metric", 0)))
     return out
 
 
 def query_from_tables(X, index, q, k, T, C_, dtab):
     """Algorithm 4 for one query with the centroid-distance tables given
     ([Ns][2][sqrtK]); the cell ranking is then taken in FP32 like the kernel's."""
-    X = _f32(X)
+    X = _columns(X, index)
+    q = _query_cols(q, index)
     n, d = X.shape
     Ns, sk = index["Ns"], index["sqrtK"]
     K = sk * sk
@@ -251,15 +297,15 @@ def query_from_tables(X, index, q, k, T, C_, dtab):
     tab = np.ascontiguousarray(dtab, dtype=np.float64).reshape(Ns, 2, sk)
     lib().orc_query_from_tables(X, n, d, Ns, sk, index["centroids"], index["cell_off"], index["perm"], _f32(q), k,
                                 int(T), int(C_), tab, oi, od, _ptr(out["scores"]), _ptr(out["cands"]),
-                                _ptr(out["teff"]), _ptr(out["activated"]))
+                                _ptr(out["teff"]), _ptr(out["activated"]), int(index.get("metric", 0)))
     return out
 
 
 def query_batch(X, index, Q, k, T, C_, rank_precision=1, nthreads=1):
     """Algorithm 4 over a batch, OpenMP over queries.  T and C_ are scalars or
     one value per query."""
-    X = _f32(X)
-    Q = _f32(Q)
+    X = _columns(X, index)
+    Q = _query_cols(Q, index)
     n, d = X.shape
     nq = Q.shape[0]
     oi = np.empty((nq, k), dtype=np.int64)
@@ -268,23 +314,32 @@ def query_batch(X, index, Q, k, T, C_, rank_precision=1, nthreads=1):
         Tq = np.ascontiguousarray(np.broadcast_to(np.asarray(T, dtype=np.int64), (nq,)))
         Cq = np.ascontiguousarray(np.broadcast_to(np.asarray(C_, dtype=np.int64), (nq,)))
         lib().orc_query_batch_pq(X, n, d, index["Ns"], index["sqrtK"], index["centroids"], index["cell_off"],
-                                 index["perm"], Q, nq, k, Tq, Cq, rank_precision, int(nthreads), oi, od)
+                                 index["perm"], Q, nq, k, Tq, Cq, rank_precision, int(nthreads), oi, od,
+                                 int(index.get("metric", 0)))
         return oi, od
     lib().orc_query_batch(X, n, d, index["Ns"], index["sqrtK"], index["centroids"], index["cell_off"],
-                          index["perm"], Q, nq, k, int(T), int(C_), rank_precision, int(nthreads), oi, od)
+                          index["perm"], Q, nq, k, int(T), int(C_), rank_precision, int(nthreads), oi, od,
+                          int(index.get("metric", 0)))
     return oi, od
 
 
-def sc_linear(X, Ns, q, k, T, C_, precision=0, cands=False):
+def sc_linear(X, Ns, q, k, T, C_, precision=0, cands=False, metric=METRIC_L2, dim_perm=None):
     """Algorithm 1 (SC-Linear).  precision 0: FP64 subspace distances; 1: the
-    kernel's FP32 arithmetic.  Returns (ids, dist, scores[, cands])."""
+    kernel's FP32 arithmetic.  metric: squared L2 or L1; dim_perm: Definition
+    3's sampling.  Returns (ids, dist, scores[, cands])."""
+    if dim_perm is not None:
+        sampled_subspaces(dim_perm, Ns)
+        pm = np.asarray(dim_perm, dtype=np.int64)
+        X = np.asarray(X, dtype=np.float32)[:, pm]
+        q = np.asarray(q, dtype=np.float32)[pm]
     X = _f32(X)
     n, d = X.shape
     oi = np.empty(k, dtype=np.int64)
     od = np.empty(k, dtype=np.float64)
     sc = np.empty(n, dtype=np.int32)
     cd = np.empty(C_, dtype=np.int64) if cands else None
-    lib().orc_sc_linear(X, n, d, Ns, _f32(q), k, int(T), int(C_), int(precision), oi, od, _ptr(sc), _ptr(cd))
+    lib().orc_sc_linear(X, n, d, Ns, _f32(q), k, int(T), int(C_), int(precision), oi, od, _ptr(sc), _ptr(cd),
+                        int(metric))
     return (oi, od, sc, cd) if cands else (oi, od, sc)
 
 

@@ -499,3 +499,107 @@ def test_sc_linear_alpha_one_and_alpha_beta_one():
     ids, dist, sc = oracle.sc_linear(X, 4, qq, 9, 800, 800, precision=1)
     ei, ed = exact_knn(X, qq, 9)
     assert ids.tolist() == ei.tolist()
+
+
+# ---------------------------------------------------------------------------
+# Variants: L1 distance (Section 5, SuCo-L1) and Definition 3's random
+# subspace sampling
+
+def _sc_linear_brute_dims(X, dims, q, T, C, metric):
+    """Algorithm 1 written from Definition 3's dim lists with library
+    routines, in either metric."""
+    n = X.shape[0]
+    scores = np.zeros(n, np.int64)
+    kind = "cityblock" if metric == 1 else "sqeuclidean"
+    for dl in dims:
+        dist = cdist(q[None, dl].astype(np.float64), X[:, dl].astype(np.float64), kind)[0]
+        scores[np.lexsort((np.arange(n), dist))[:T]] += 1
+    return scores, np.lexsort((np.arange(n), -scores))[:C]
+
+
+def test_sampled_subspaces_follow_definition_3():
+    rng = np.random.default_rng(91)
+    perm = rng.permutation(23)
+    dims = oracle.sampled_subspaces(perm, 4)
+    assert [len(x) for x in dims] == [5, 5, 5, 8]              # floor(23/4), the last takes the rest
+    assert sorted(np.concatenate(dims).tolist()) == list(range(23))
+    with pytest.raises(AssertionError):
+        oracle.sampled_subspaces([0, 1, 1, 3], 2)
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_sc_linear_with_sampled_subspaces_and_metric_against_brute_force(metric):
+    X = W.dataset(1, n=2000)
+    perm = np.random.default_rng(92).permutation(X.shape[1])
+    dims = oracle.sampled_subspaces(perm, 8)
+    for qq in W.queries(1, nq=3):
+        ids, dist, sc, cands = oracle.sc_linear(X, 8, qq, 10, 100, 40, precision=0, cands=True, metric=metric,
+                                                dim_perm=perm)
+        bs, bc = _sc_linear_brute_dims(X, dims, qq, 100, 40, metric)
+        np.testing.assert_array_equal(sc, bs)
+        assert sorted(cands.tolist()) == sorted(bc.tolist())
+
+
+def test_l1_query_alpha_beta_one_is_exact_l1_knn():
+    X = W.dataset(1, n=1500)
+    idx = oracle.build_index(X, 4, 4, 3, W.random_init_ids(93, 1500, 4, 4), metric=1)
+    for qq in W.queries(1, nq=3):
+        o = oracle.query(X, idx, qq, 10, T=1500, C_=1500, rank_precision=0)
+        d = cdist(qq[None, :].astype(np.float64), X.astype(np.float64), "cityblock")[0]
+        order = np.lexsort((np.arange(len(d)), d))[:10]
+        assert o["ids"].tolist() == order.tolist()
+        np.testing.assert_allclose(o["dist"], d[order], rtol=1e-12)
+        assert (o["scores"] == 4).all()
+
+
+def test_l1_kmeans_assignment_is_the_l1_argmin():
+    X = W.dataset(1, n=1200)
+    init = np.arange(0, 1200, 100)
+    cent, assign = oracle.kmeans(X, 8, 8, len(init), 1, init, metric=1)
+    # after one step: the assignment used the initial points, by L1
+    d = cdist(X[:, 8:16].astype(np.float64), X[init][:, 8:16].astype(np.float64), "cityblock")
+    np.testing.assert_array_equal(assign, d.argmin(axis=1))
+    for a in range(len(init)):
+        if (assign == a).any():
+            np.testing.assert_allclose(cent[a], X[assign == a][:, 8:16].astype(np.float64).mean(0), rtol=1e-12)
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_suco_equals_sc_linear_on_a_product_grid_in_both_metrics(metric):
+    # every cell holds one point on its product centroid: the cell value is the
+    # point's exact subspace distance (in L1 as well: it is additive)
+    rng = np.random.default_rng(94)
+    Ns, sk, hl = 3, 7, 2
+    d, n = Ns * 2 * hl, sk * sk
+    cents = rng.random((Ns, 2, sk, hl)).astype(np.float32)
+    X = np.empty((n, d), np.float32)
+    assign = np.empty((Ns, 2, n), np.int32)
+    for i in range(Ns):
+        cells = rng.permutation(n)
+        for p in range(n):
+            a1, a2 = divmod(int(cells[p]), sk)
+            X[p, i * 2 * hl:i * 2 * hl + hl] = cents[i, 0, a1]
+            X[p, i * 2 * hl + hl:(i + 1) * 2 * hl] = cents[i, 1, a2]
+            assign[i, 0, p], assign[i, 1, p] = a1, a2
+    idx = oracle.index_from_parts(Ns, sk, cents, assign, metric=metric)
+    for qq in rng.random((4, d)).astype(np.float32):
+        a = oracle.query(X, idx, qq, 5, 12, 10, rank_precision=0)
+        ids, dist, sc = oracle.sc_linear(X, Ns, qq, 5, 12, 10, metric=metric)
+        assert (a["scores"] == sc).all()
+        assert a["ids"].tolist() == ids.tolist()
+
+
+def test_sampling_that_only_reorders_dims_inside_halves_changes_nothing_on_exact_data():
+    # Definition 3 treats a subspace as a set of dims: reordering the dims of
+    # each half (integer data, exact in FP64) leaves every stage unchanged
+    X = W.random_data(95, 2000, 16, kind="int")
+    rng = np.random.default_rng(96)
+    perm = np.concatenate([rng.permutation(np.arange(h * 2, h * 2 + 2)) for h in range(8)])  # 4 subspaces, halves of 2
+    init = W.random_init_ids(97, 2000, 4, 5)
+    a = oracle.build_index(X, 4, 5, 0, init)
+    b = oracle.build_index(X, 4, 5, 0, init, dim_perm=perm)
+    for qq in W.random_data(98, 4, 16, kind="int"):
+        oa = oracle.query(X, a, qq, 8, 100, 30, rank_precision=0)
+        ob = oracle.query(X, b, qq, 8, 100, 30, rank_precision=0)
+        for key in ("teff", "activated", "scores", "ids", "dist"):
+            np.testing.assert_array_equal(oa[key], ob[key], err_msg=key)
