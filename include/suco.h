@@ -63,15 +63,33 @@ extern "C" {
 
 typedef struct suco_index suco_index; /* opaque; owned by the library */
 
+/* Distance of an index (suco_build_params.metric).  L2: squared Euclidean,
+ * the paper's default.  L1: Manhattan, the variant of Section 5's
+ * distance-measure experiment (SuCo-L1): half-subspace centroid distances,
+ * cell values d1 + d2 (L1 is a sum over dims, so this is the distance to the
+ * product centroid), K-means assignments and the re-rank all use it, and
+ * result distances are L1 distances.  An L1 index takes only FP32 ranking and
+ * re-rank (the tensor-core and coarse forms are squared-L2 expansions) and
+ * CTAs of 512 threads. */
+#define SUCO_METRIC_L2 0
+#define SUCO_METRIC_L1 1
+
 /* Index construction parameters (Algorithm 2). */
 typedef struct suco_build_params {
     int32_t Ns;              /* number of subspaces, 1..32                              */
     int32_t sqrtK;           /* centroids per half-subspace codebook, 1..256, <= n      */
     int32_t kmeans_iters;    /* Lloyd iterations t (0 keeps the initial points)        */
-    int32_t reserved0;       /* must be 0                                              */
+    int32_t metric;          /* SUCO_METRIC_L2 (0) or SUCO_METRIC_L1                   */
     uint64_t seed;           /* seeds the initial-centroid draw when init_ids is NULL  */
     const int64_t* init_ids; /* (host, nullable) [Ns][2][sqrtK] distinct point ids that
                                 seed Lloyd's iterations, one list per half-subspace      */
+    const int32_t* dim_perm; /* (host, nullable) Definition 3's subspace sampling: a
+                                permutation of [0, d); subspace i < Ns-1 takes dims
+                                dim_perm[i*s .. (i+1)*s) (s = floor(d/Ns)), the last the
+                                rest, each half the first floor(len/2) of its list and
+                                then the rest.  NULL: contiguous subspaces (Section 3.2).
+                                The index stores D with its columns in this order, and
+                                queries are read through it.                          */
 } suco_build_params;
 
 /* Builds the index of Algorithm 2 on the GPU: K-means per half-subspace
@@ -100,6 +118,16 @@ SUCO_API int suco_build_index(const float* data, int64_t n, int32_t d, const suc
 SUCO_API int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
                                       const float* centroids, const int32_t* assign, void* stream,
                                       suco_index** out);
+
+/* The IMI part of Algorithm 2 from given centroids and assignments, for any
+ * metric and subspace sampling of `params` (Ns, sqrtK, metric, dim_perm;
+ * kmeans_iters, seed and init_ids are ignored).
+ *   centroids  (host) [Ns][2][sqrtK][hmax] FP32 over each half's dims in the
+ *              sampling's order.   assign  (host) [Ns][2][n] int32 in [0, sqrtK).
+ * Synchronous.  Errors: as suco_build_index_from_assignments. */
+SUCO_API int suco_build_index_from_parts(const float* data, int64_t n, int32_t d, const suco_build_params* params,
+                                         const float* centroids, const int32_t* assign, void* stream,
+                                         suco_index** out);
 
 /* Query parameters (Algorithm 4).  The three per-query arrays are optional;
  * a query without an array entry uses the scalar.  With per-query values the
@@ -167,7 +195,8 @@ typedef struct suco_query_params {
 } suco_query_params;
 
 /* Answers nq queries (Algorithm 4; Algorithm 3 for the cell walk).
- *   queries   (device) nq x d FP32 row-major.
+ *   queries   (device) nq x d FP32 row-major (in the original dim order; a
+ *             sampled index reads them through its permutation).
  *   out_ids   (device) nq x k int32: ids by ascending squared distance (ties
  *             by id); -1 where fewer than k candidates exist (only if n < k).
  *   out_dist  (device) nq x k FP32 squared Euclidean distances; +inf padding.
@@ -326,6 +355,8 @@ typedef struct suco_index_info {
     int64_t K;         /* sqrtK^2 cells per subspace                            */
     int64_t ld;        /* row stride of the index's copy of D, in floats        */
     int64_t device_bytes;
+    int32_t metric;    /* SUCO_METRIC_*                                         */
+    int32_t sampled;   /* 1 when the subspaces follow a dim_perm                */
 } suco_index_info;
 
 SUCO_API int suco_index_get_info(const suco_index* index, suco_index_info* info);

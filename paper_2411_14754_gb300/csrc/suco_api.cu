@@ -95,6 +95,8 @@ namespace {
 
 void free_index_memory(DeviceIndex* ix)
 {
+    cudaFree(ix->dperm);
+    ix->dperm = nullptr;
     cudaFree(ix->X);
     cudaFree(ix->cent);
     cudaFree(ix->cell_off);
@@ -131,9 +133,34 @@ int check_sizes(int64_t n, int32_t d, int32_t Ns, int32_t sqrtK)
     return SUCO_OK;
 }
 
-// Allocates the index arrays and copies the dataset (zero-padded to ld).
-int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK, cudaStream_t st)
+// X[p][j] = data[p][perm[j]]: the dataset's columns in the sampling's order
+__global__ void gather_columns_kernel(const float* __restrict__ data, int64_t n, int32_t d,
+                                      const int32_t* __restrict__ perm, float* __restrict__ X, int64_t ld)
 {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * ld; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / ld;
+        const int j = (int)(t - p * ld);
+        X[t] = j < d ? data[p * d + perm[j]] : 0.f;
+    }
+}
+
+int check_perm(const int32_t* perm, int32_t d)
+{
+    std::vector<char> seen((size_t)d, 0);
+    for (int32_t j = 0; j < d; ++j) {
+        if (perm[j] < 0 || perm[j] >= d || seen[(size_t)perm[j]])
+            return fail(SUCO_EINVAL, "dim_perm is not a permutation of [0, %d) (entry %d = %d)", d, j, perm[j]);
+        seen[(size_t)perm[j]] = 1;
+    }
+    return SUCO_OK;
+}
+
+// Allocates the index arrays and copies the dataset (zero-padded to ld; with
+// a dim_perm, its columns in the sampling's order).
+int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
+                const int32_t* dim_perm, int32_t metric, cudaStream_t st)
+{
+    ix->metric = metric;
     ix->n = n;
     ix->d = d;
     ix->Ns = Ns;
@@ -187,6 +214,23 @@ int alloc_index(DeviceIndex* ix, const float* data, int64_t n, int32_t d, int32_
     }
     SUCO_CUDA_TRY(cudaMemsetAsync(ix->cent, 0, a[1].b, st));
     SUCO_CUDA_TRY(cudaMemsetAsync(ix->work, 0, a[5].b, st));
+    if (dim_perm) {
+        cudaError_t err = fault_fires(SUCO_FAULT_ALLOC) ? cudaErrorMemoryAllocation
+                                                        : cudaMalloc(&ix->dperm, (size_t)d * 4);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            ix->dperm = nullptr;
+            free_index_memory(ix);
+            return fail(SUCO_ENOMEM, "cudaMalloc of the dim permutation failed: %s", cudaGetErrorString(err));
+        }
+        ix->bytes += (int64_t)d * 4;
+        SUCO_CUDA_TRY(cudaMemcpyAsync(ix->dperm, dim_perm, (size_t)d * 4, cudaMemcpyHostToDevice, st));
+        gather_columns_kernel<<<(unsigned)std::min<int64_t>((n * ix->ld + 255) / 256, 152 * 64), 256, 0, st>>>(
+            data, n, d, ix->dperm, ix->X, ix->ld);
+        SUCO_LAUNCH_CHECK("gather_columns_kernel");
+        SUCO_CUDA_TRY(cudaStreamSynchronize(st));  // the host copy of dim_perm is the caller's
+        return SUCO_OK;
+    }
     if (ix->ld != d) SUCO_CUDA_TRY(cudaMemsetAsync(ix->X, 0, a[0].b, st));
     SUCO_CUDA_TRY(cudaMemcpy2DAsync(ix->X, (size_t)ix->ld * 4, data, (size_t)d * 4, (size_t)d * 4, (size_t)n,
                                     cudaMemcpyDeviceToDevice, st));
@@ -220,6 +264,13 @@ int check_query_params(const suco_index* index, const float* queries, int64_t nq
     if (p->rank_precision == SUCO_RANK_FP8 && !index->ix.s8col)
         return fail(SUCO_ESTATE, "FP8 ranking uses the scales of the FP8 copy: call suco_add_reduced_copies with "
                                  "SUCO_COPY_FP8 first");
+    if (index->ix.metric == SUCO_METRIC_L1) {
+        if (p->precision != SUCO_PRECISION_FP32 || p->rank_precision != SUCO_RANK_FP32)
+            return fail(SUCO_EUNSUPPORTED, "an L1 index ranks and re-ranks in FP32 only (the tensor-core and coarse "
+                                           "forms expand the squared Euclidean distance)");
+        if (p->threads != 0 && p->threads != 512)
+            return fail(SUCO_EUNSUPPORTED, "an L1 index runs CTAs of 512 threads (threads = 0 or 512)");
+    }
     if (p->exact_rerank < 0 || p->exact_rerank > (1 << 24))
         return fail(SUCO_EINVAL, "exact_rerank=%d must be in [0, 2^24]", p->exact_rerank);
     if (nq > 0 && (!queries || !ids || !dist)) return fail(SUCO_EINVAL, "queries/out_ids/out_dist must not be NULL");
@@ -243,7 +294,9 @@ int suco_build_index(const float* data, int64_t n, int32_t d, const suco_build_p
     if (rc) return rc;
     if (params->kmeans_iters < 0 || params->kmeans_iters > 10000)
         return fail(SUCO_EINVAL, "kmeans_iters=%d must be in [0, 10000]", params->kmeans_iters);
-    if (params->reserved0 != 0) return fail(SUCO_EINVAL, "reserved0 must be 0");
+    if (params->metric != SUCO_METRIC_L2 && params->metric != SUCO_METRIC_L1)
+        return fail(SUCO_EINVAL, "metric=%d must be SUCO_METRIC_L2 or SUCO_METRIC_L1", params->metric);
+    if (params->dim_perm && (rc = check_perm(params->dim_perm, d))) return rc;
     const int Ns = params->Ns, sk = params->sqrtK;
     std::vector<int64_t> init((size_t)2 * Ns * sk);
     if (params->init_ids) {
@@ -271,7 +324,7 @@ int suco_build_index(const float* data, int64_t n, int32_t d, const suco_build_p
     cudaStream_t st = (cudaStream_t)stream;
     suco_index* idx = fault_fires(SUCO_FAULT_ALLOC) ? nullptr : new (std::nothrow) suco_index();
     if (!idx) return fail(SUCO_ENOMEM, "host allocation failed");
-    rc = alloc_index(&idx->ix, data, n, d, Ns, sk, st);
+    rc = alloc_index(&idx->ix, data, n, d, Ns, sk, params->dim_perm, params->metric, st);
     if (!rc) rc = kmeans_build(&idx->ix, init.data(), params->kmeans_iters, st);
     if (rc) {
         cudaStreamSynchronize(st);
@@ -283,14 +336,18 @@ int suco_build_index(const float* data, int64_t n, int32_t d, const suco_build_p
     return SUCO_OK;
 }
 
-int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
-                                      const float* centroids, const int32_t* assign, void* stream, suco_index** out)
+int suco_build_index_from_parts(const float* data, int64_t n, int32_t d, const suco_build_params* params,
+                                const float* centroids, const int32_t* assign, void* stream, suco_index** out)
 {
     clear_error();
-    if (!data || !centroids || !assign || !out) return fail(SUCO_EINVAL, "pointers must not be NULL");
+    if (!data || !params || !centroids || !assign || !out) return fail(SUCO_EINVAL, "pointers must not be NULL");
     *out = nullptr;
+    const int32_t Ns = params->Ns, sqrtK = params->sqrtK;
     int rc = check_sizes(n, d, Ns, sqrtK);
     if (rc) return rc;
+    if (params->metric != SUCO_METRIC_L2 && params->metric != SUCO_METRIC_L1)
+        return fail(SUCO_EINVAL, "metric=%d must be SUCO_METRIC_L2 or SUCO_METRIC_L1", params->metric);
+    if (params->dim_perm && (rc = check_perm(params->dim_perm, d))) return rc;
     for (int64_t t = 0; t < (int64_t)2 * Ns * n; ++t)
         if (assign[t] < 0 || assign[t] >= sqrtK)
             return fail(SUCO_EINVAL, "assign[%lld] = %d out of [0, %d)", (long long)t, assign[t], sqrtK);
@@ -298,7 +355,7 @@ int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, i
     suco_index* idx = fault_fires(SUCO_FAULT_ALLOC) ? nullptr : new (std::nothrow) suco_index();
     if (!idx) return fail(SUCO_ENOMEM, "host allocation failed");
     DeviceIndex* ix = &idx->ix;
-    rc = alloc_index(ix, data, n, d, Ns, sqrtK, st);
+    rc = alloc_index(ix, data, n, d, Ns, sqrtK, params->dim_perm, params->metric, st);
     DevBuf dassign;
     std::vector<float> cent;
     if (!rc) {
@@ -328,6 +385,16 @@ int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, i
     }
     *out = idx;
     return SUCO_OK;
+}
+
+int suco_build_index_from_assignments(const float* data, int64_t n, int32_t d, int32_t Ns, int32_t sqrtK,
+                                      const float* centroids, const int32_t* assign, void* stream, suco_index** out)
+{
+    suco_build_params p;
+    memset(&p, 0, sizeof(p));
+    p.Ns = Ns;
+    p.sqrtK = sqrtK;
+    return suco_build_index_from_parts(data, n, d, &p, centroids, assign, stream, out);
 }
 
 int suco_query_batch(const suco_index* index, const float* queries, int64_t nq, const suco_query_params* params,
@@ -420,6 +487,8 @@ int suco_index_get_info(const suco_index* index, suco_index_info* info)
     info->K = ix.K;
     info->ld = ix.ld;
     info->device_bytes = ix.bytes;
+    info->metric = ix.metric;
+    info->sampled = ix.dperm != nullptr;
     return SUCO_OK;
 }
 

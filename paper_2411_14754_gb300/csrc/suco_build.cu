@@ -3,7 +3,9 @@
 //   (IMI) of every subspace as a CSR of ids grouped by cell.
 //
 // K-means details the paper leaves open (Algorithm 2 only calls "Kmeans"):
-// initial centroids are given point ids; an empty cluster keeps its centroid;
+// initial centroids are given point ids; assignments take the index's
+// distance (squared Euclidean, or L1 for an L1 index) and updates the member
+// means; an empty cluster keeps its centroid;
 // argmin ties go to the lowest centroid index; the final assignment that
 // defines the IMI is taken against the final centroids.  Centroid sums are
 // accumulated in 64-bit fixed point so that the build is bitwise
@@ -50,10 +52,18 @@ __global__ void maxabs_kernel(const float* __restrict__ X, int64_t ld, int64_t n
     if ((threadIdx.x & 31) == 0) atomicMax(out + ih, __float_as_uint(m));
 }
 
-// Nearest centroid of every point in one half-subspace (grid.y = half).
+// One dimension's term of the index's distance, accumulated in FP32:
+// squared Euclidean by one fused multiply-add, L1 by one addition.
+__device__ __forceinline__ float dist_term(float acc, float df, int metric)
+{
+    return metric == SUCO_METRIC_L1 ? __fadd_rn(acc, fabsf(df)) : __fmaf_rn(df, df, acc);
+}
+
+// Nearest centroid of every point in one half-subspace (grid.y = half), in
+// the index's metric.
 __global__ void kmeans_assign_kernel(const float* __restrict__ X, int64_t ld, int64_t n, int32_t d, int32_t Ns,
                                      int32_t sub_s, int32_t sqrtK, int32_t hmax, const float* __restrict__ cent,
-                                     int32_t* __restrict__ assign)
+                                     int32_t* __restrict__ assign, int metric)
 {
     extern __shared__ float s_cent[];  // sqrtK * len
     const int ih = blockIdx.y;
@@ -78,10 +88,7 @@ __global__ void kmeans_assign_kernel(const float* __restrict__ X, int64_t ld, in
                 float acc = 0.f;
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                    if (j < len) {
-                        const float df = __fsub_rn(xr[j], c[j]);
-                        acc = __fmaf_rn(df, df, acc);
-                    }
+                    if (j < len) acc = dist_term(acc, __fsub_rn(xr[j], c[j]), metric);
                 if (acc < bd) {
                     bd = acc;
                     best = a;
@@ -91,10 +98,7 @@ __global__ void kmeans_assign_kernel(const float* __restrict__ X, int64_t ld, in
             for (int a = 0; a < sqrtK; ++a) {
                 const float* c = s_cent + a * len;
                 float acc = 0.f;
-                for (int j = 0; j < len; ++j) {
-                    const float df = __fsub_rn(__ldg(x + j), c[j]);
-                    acc = __fmaf_rn(df, df, acc);
-                }
+                for (int j = 0; j < len; ++j) acc = dist_term(acc, __fsub_rn(__ldg(x + j), c[j]), metric);
                 if (acc < bd) {
                     bd = acc;
                     best = a;
@@ -323,7 +327,7 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
     const dim3 g_accum(grid_for(n, 256, 2 * nsm), H);
     for (int it = 0; it < iters; ++it) {
         kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm,
-                                                                ix->cent, assign.as<int32_t>());
+                                                                ix->cent, assign.as<int32_t>(), ix->metric);
         SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
         SUCO_CUDA_TRY(cudaMemsetAsync(gsum.p, 0, gsum.bytes, st));
         SUCO_CUDA_TRY(cudaMemsetAsync(gcnt.p, 0, gcnt.bytes, st));
@@ -338,7 +342,7 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
     }
     // the assignment that defines the IMI, against the final centroids
     kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm, ix->cent,
-                                                            assign.as<int32_t>());
+                                                            assign.as<int32_t>(), ix->metric);
     SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
     return build_imi(ix, assign.as<int32_t>(), st);
 }
@@ -450,7 +454,8 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
     const dim3 g_assign(grid_for(n, 256, 8 * nsm), 1);
     const dim3 g_accum(grid_for(n, 256, 2 * nsm), 1);
     for (int it = 0; it < iters; ++it) {
-        kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign);
+        kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign,
+                                                                SUCO_METRIC_L2);
         SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
         // sums and counts start from zero in every iteration (the array keeps the last call's contents)
         SUCO_CUDA_TRY(cudaMemsetAsync(gsum, 0, (size_t)k * dim_len * 8, st));
@@ -463,7 +468,8 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
         SUCO_LAUNCH_CHECK("kmeans_finalize_kernel");
     }
     // the assignment against the final centroids
-    kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign);
+    kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign,
+                                                            SUCO_METRIC_L2);
     SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
     return SUCO_OK;
 }

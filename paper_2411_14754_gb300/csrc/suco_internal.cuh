@@ -57,6 +57,10 @@ struct DeviceIndex {
     // reads status_host without synchronising
     volatile uint32_t* status_host = nullptr;
     uint32_t* status_dev = nullptr;
+    int32_t metric = SUCO_METRIC_L2;
+    // Definition 3's subspace sampling: X holds column dperm[j] of D at column
+    // j, so every sampled subspace is contiguous; queries are read through it
+    int32_t* dperm = nullptr;     // device [d], or null for contiguous subspaces
     int device = 0;
     int64_t bytes = 0;
     // launch shapes chosen by suco_autotune, per (k, candidate bound C)
@@ -104,6 +108,11 @@ struct DevBuf {
 
 int build_imi(DeviceIndex* ix, const int32_t* assign_dev /*[Ns][2][n]*/, cudaStream_t st);
 int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, cudaStream_t st);
+// the query value a kernel stages at column j of a (possibly sampled) index
+__device__ __forceinline__ float query_col(const float* q_row, const int32_t* dperm, int j)
+{
+    return q_row[dperm ? __ldg(dperm + j) : j];
+}
 int rank_tc_tables(const DeviceIndex* ix, const float* Q, int64_t nq, float* D, bool fp8, cudaStream_t st);
 int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_query_params* p, int32_t* ids,
                  float* dist, const suco_query_debug_out* dbg, cudaStream_t st);

@@ -2,8 +2,8 @@
 // its conclusion names learning as future work).
 //
 // A small MLP reads per-query features taken from the same centroid distances
-// that drive the cell ranking (Section 4.2, Algorithm 4 lines computing
-// dists1/dists2): for each subspace i the smallest squared distance to a
+// that drive the cell ranking (Section 4.2, Algorithm 4's half-subspace
+// distances, in the index's metric): for each subspace i the smallest distance to a
 // first-half centroid, the smallest to a second-half centroid, and
 // log(1 + size of the IMI cell formed by the two nearest centroids).  It
 // predicts (log alpha, log beta); the query path then uses them per query.
@@ -40,13 +40,14 @@ __device__ __forceinline__ float bf(const uint16_t* p, size_t i)
 // Features of one query (block per query).  dist: [Ns][2][sqrtK] in shared memory.
 __global__ void features_kernel(const float* __restrict__ cent, const uint32_t* __restrict__ cell_off, int32_t d,
                                 int32_t Ns, int32_t sub_s, int32_t sqrtK, int32_t hmax, int64_t K,
-                                const float* __restrict__ Q, int64_t nq, float* __restrict__ feats)
+                                const float* __restrict__ Q, int64_t nq, float* __restrict__ feats,
+                                const int32_t* __restrict__ qperm, int metric)
 {
     extern __shared__ float sh[];
     float* qs = sh;              // [d]
     float* dist = sh + d;        // [Ns][2][sqrtK]
     const int64_t b = blockIdx.x;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) qs[j] = Q[b * d + j];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) qs[j] = query_col(Q + b * d, qperm, j);
     __syncthreads();
     const int npair = Ns * 2 * sqrtK;
     for (int t = threadIdx.x; t < npair; t += blockDim.x) {
@@ -57,7 +58,7 @@ __global__ void features_kernel(const float* __restrict__ cent, const uint32_t* 
         float acc = 0.f;
         for (int j = 0; j < len; ++j) {
             const float df = __fsub_rn(qs[off + j], __ldg(c + j));
-            acc = __fmaf_rn(df, df, acc);
+            acc = metric == SUCO_METRIC_L1 ? __fadd_rn(acc, fabsf(df)) : __fmaf_rn(df, df, acc);
         }
         dist[t] = acc;
     }
@@ -231,7 +232,8 @@ __global__ void predict_kernel(MlpDev M, const float* __restrict__ cent, const u
                                int32_t d, int32_t Ns, int32_t sub_s, int32_t sqrtK, int32_t hmax, int64_t K,
                                const float* __restrict__ Q, int64_t nq, float off0, float off1, float la_lo,
                                float la_hi, float lb_lo, float lb_hi, float fb_alpha, float fb_beta,
-                               float* __restrict__ alpha, float* __restrict__ beta, float* __restrict__ feats_scratch)
+                               float* __restrict__ alpha, float* __restrict__ beta, float* __restrict__ feats_scratch,
+                               const int32_t* __restrict__ qperm, int metric)
 {
     // the features of this query land in feats_scratch[b] first
     extern __shared__ float sh[];
@@ -240,7 +242,7 @@ __global__ void predict_kernel(MlpDev M, const float* __restrict__ cent, const u
     float* xn = dist + Ns * 2 * sqrtK;   // [F]
     float* fx = xn + 3 * Ns;             // [F]
     const int64_t b = blockIdx.x;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) qs[j] = Q[b * d + j];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) qs[j] = query_col(Q + b * d, qperm, j);
     __syncthreads();
     const int npair = Ns * 2 * sqrtK;
     for (int t = threadIdx.x; t < npair; t += blockDim.x) {
@@ -251,7 +253,7 @@ __global__ void predict_kernel(MlpDev M, const float* __restrict__ cent, const u
         float acc = 0.f;
         for (int j = 0; j < len; ++j) {
             const float df = __fsub_rn(qs[off + j], __ldg(c + j));
-            acc = __fmaf_rn(df, df, acc);
+            acc = metric == SUCO_METRIC_L1 ? __fadd_rn(acc, fabsf(df)) : __fmaf_rn(df, df, acc);
         }
         dist[t] = acc;
     }
@@ -345,7 +347,8 @@ int suco_query_features(const suco_index* index, const float* queries, int64_t n
     if (smem > 200 * 1024) return fail(SUCO_EUNSUPPORTED, "feature tables of %zu bytes exceed shared memory", smem);
     SUCO_CUDA_TRY(cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     features_kernel<<<(unsigned)nq, 128, smem, (cudaStream_t)stream>>>(ix.cent, ix.cell_off, ix.d, ix.Ns, ix.sub_s,
-                                                                      ix.sqrtK, ix.hmax, ix.K, queries, nq, feats);
+                                                                      ix.sqrtK, ix.hmax, ix.K, queries, nq, feats,
+                                                                      ix.dperm, ix.metric);
     SUCO_LAUNCH_CHECK("features_kernel");
     return SUCO_OK;
 }
@@ -369,7 +372,7 @@ int suco_mlp_predict(const suco_index* index, const suco_mlp* model, const float
     predict_kernel<<<(unsigned)nq, 128, smem, (cudaStream_t)stream>>>(
         M, ix.cent, ix.cell_off, ix.d, ix.Ns, ix.sub_s, ix.sqrtK, ix.hmax, ix.K, queries, nq, model->out_offset[0],
         model->out_offset[1], model->log_alpha_min, model->log_alpha_max, model->log_beta_min, model->log_beta_max,
-        model->fallback_alpha, model->fallback_beta, alpha, beta, nullptr);
+        model->fallback_alpha, model->fallback_beta, alpha, beta, nullptr, ix.dperm, ix.metric);
     SUCO_LAUNCH_CHECK("predict_kernel");
     return SUCO_OK;
 }

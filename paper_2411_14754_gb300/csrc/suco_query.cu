@@ -104,6 +104,7 @@ struct QArgs {
     const uint8_t* __restrict__ X8;    // FP8 E4M3 copy of X / column scale, [n][ld8] (precision 2)
     int64_t ld8;
     const float* __restrict__ s8col;   // [ld8] column scales of the FP8 copy
+    const int32_t* __restrict__ qperm;   // Definition 3 sampling: staged query column j = q[qperm[j]] (or null)
     int32_t* out_ids;
     float* out_dist;
     int64_t* dbg_teff;
@@ -212,6 +213,14 @@ __device__ __forceinline__ void stamp(const QArgs& A, int64_t b, uint32_t r, int
 }
 
 // ---------------------------------------------------------------------------
+
+// One dimension's term of the index's distance in FP32: squared Euclidean by
+// one fused multiply-add (MET 0), Manhattan by one addition (MET 1).
+template <int MET>
+__device__ __forceinline__ float dterm(float acc, float df)
+{
+    return MET == 1 ? __fadd_rn(acc, fabsf(df)) : __fmaf_rn(df, df, acc);
+}
 
 // Cell key of Algorithm 3's retrieval order: FP32 cell sum, then the ranks.
 __device__ __forceinline__ unsigned long long cell_key(float a, float b, uint32_t r1, uint32_t r2)
@@ -453,7 +462,7 @@ __device__ __forceinline__ int value_bucket(float s, float smin, float scale)
 // one half of it when the CTA ranks two subspaces at once (tid within the
 // half, named barrier 1 or 2, scratch group 0 or 1: its own S3 area of the
 // union, its own o_hist histograms and o_misc slots).
-template <int NT>
+template <int NT, int MET>
 __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint32_t T, int tid, int bar, int grp)
 {
     const int sk = A.sqrtK;
@@ -494,16 +503,10 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
         float acc = 0.f;
         if (A.stage_cent) {
             const float* c = cst + h * A.hmax * sk + a;
-            for (int j = 0; j < len; ++j) {
-                const float df = __fsub_rn(qs[off + j], c[j * sk]);
-                acc = __fmaf_rn(df, df, acc);
-            }
+            for (int j = 0; j < len; ++j) acc = dterm<MET>(acc, __fsub_rn(qs[off + j], c[j * sk]));
         } else {
             const float* c = cg + (int64_t)(h * sk + a) * A.hmax;
-            for (int j = 0; j < len; ++j) {
-                const float df = __fsub_rn(qs[off + j], __ldg(c + j));
-                acc = __fmaf_rn(df, df, acc);
-            }
+            for (int j = 0; j < len; ++j) acc = dterm<MET>(acc, __fsub_rn(qs[off + j], __ldg(c + j)));
         }
         (h ? tb.d2 : tb.d1)[a] = acc;
     }
@@ -1009,7 +1012,7 @@ __device__ __forceinline__ uint32_t bitsliced_ge(const uint32_t acc[B], uint32_t
 // into keys (distance bits << 32 | id; ~0 for an id outside [0, n)).  8 lanes
 // per row, two groups of 4 rows per warp in flight; each lane keeps S6_CH
 // float4 chunks of each of its two rows in registers per load round.
-template <int NT, int S6_CH>
+template <int NT, int S6_CH, int MET>
 __device__ void rerank_fp32(const QArgs& A, const float4* q4, const uint32_t* ids, uint32_t count,
                             unsigned long long* keys)
 {
@@ -1043,22 +1046,14 @@ __device__ void rerank_fp32(const QArgs& A, const float4* q4, const uint32_t* id
                 const int c = c0 + 8 * u;
                 if (c < ld4) {
                     const float4 qv = q4[c];
-                    float df = __fsub_rn(xa[u].x, qv.x);
-                    acc_a = __fmaf_rn(df, df, acc_a);
-                    df = __fsub_rn(xa[u].y, qv.y);
-                    acc_a = __fmaf_rn(df, df, acc_a);
-                    df = __fsub_rn(xa[u].z, qv.z);
-                    acc_a = __fmaf_rn(df, df, acc_a);
-                    df = __fsub_rn(xa[u].w, qv.w);
-                    acc_a = __fmaf_rn(df, df, acc_a);
-                    df = __fsub_rn(xc[u].x, qv.x);
-                    acc_c = __fmaf_rn(df, df, acc_c);
-                    df = __fsub_rn(xc[u].y, qv.y);
-                    acc_c = __fmaf_rn(df, df, acc_c);
-                    df = __fsub_rn(xc[u].z, qv.z);
-                    acc_c = __fmaf_rn(df, df, acc_c);
-                    df = __fsub_rn(xc[u].w, qv.w);
-                    acc_c = __fmaf_rn(df, df, acc_c);
+                    acc_a = dterm<MET>(acc_a, __fsub_rn(xa[u].x, qv.x));
+                    acc_a = dterm<MET>(acc_a, __fsub_rn(xa[u].y, qv.y));
+                    acc_a = dterm<MET>(acc_a, __fsub_rn(xa[u].z, qv.z));
+                    acc_a = dterm<MET>(acc_a, __fsub_rn(xa[u].w, qv.w));
+                    acc_c = dterm<MET>(acc_c, __fsub_rn(xc[u].x, qv.x));
+                    acc_c = dterm<MET>(acc_c, __fsub_rn(xc[u].y, qv.y));
+                    acc_c = dterm<MET>(acc_c, __fsub_rn(xc[u].z, qv.z));
+                    acc_c = dterm<MET>(acc_c, __fsub_rn(xc[u].w, qv.w));
                 }
             }
         }
@@ -1313,7 +1308,7 @@ __device__ unsigned long long cluster_rank_cut(const QArgs& A, char* smem, const
     return prefix;
 }
 
-template <int NT, int NSMAX>
+template <int NT, int NSMAX, int MET>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_query_kernel(const QArgs A)
 {
     extern __shared__ __align__(16) char smem[];
@@ -1381,7 +1376,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
             q_next = false;
         } else {
             const float* qg = A.Q + b * A.d;
-            for (int j = threadIdx.x; j < A.ldq; j += NT) qs[j] = j < A.d ? qg[j] : 0.f;
+            for (int j = threadIdx.x; j < A.ldq; j += NT) qs[j] = j < A.d ? query_col(qg, A.qperm, j) : 0.f;
         }
         uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + A.o_cnt);
         for (int t = threadIdx.x; t < 2 * NC; t += NT) cnt[t] = 0u;
@@ -1394,10 +1389,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     if (A.pair_ok && (int)r + CL < A.Ns && (int)r + 2 * CL >= A.Ns) {
         // two subspaces: each half of the CTA ranks one (named barriers 1, 2)
         const int grp = threadIdx.x >= NT / 2;
-        rank_subspace<NT / 2>(A, smem, b, (int)r + grp * CL, qT, (int)threadIdx.x - grp * (NT / 2), 1 + grp, grp);
+        rank_subspace<NT / 2, MET>(A, smem, b, (int)r + grp * CL, qT, (int)threadIdx.x - grp * (NT / 2), 1 + grp,
+                                   grp);
         __syncthreads();  // both halves are done with their scratch before the union is cleared
     } else {
-        for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT>(A, smem, b, i, qT, (int)threadIdx.x, 0, 0);
+        for (int i = (int)r; i < A.Ns; i += CL) rank_subspace<NT, MET>(A, smem, b, i, qT, (int)threadIdx.x, 0, 0);
     }
     stamp(A, b, r, 3);
     // clear the bit planes (the union region served as S3 scratch)
@@ -1735,7 +1731,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         if (A.o_qn && bn < A.nq) {
             const float* qg = A.Q + bn * A.d;
             float* qn = reinterpret_cast<float*>(smem + A.o_qn);
-            for (int j = threadIdx.x; j < A.d; j += NT) cp_async4(qn + j, qg + j);
+            for (int j = threadIdx.x; j < A.d; j += NT) cp_async4(qn + j, qg + (A.qperm ? A.qperm[j] : j));
             q_next = true;
         }
     }
@@ -1744,13 +1740,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem + A.o_keys);  // [sortP]
     const float4* q4 = reinterpret_cast<const float4*>(smem + A.o_q);
     uint32_t nk = mine;  // keys of this CTA that enter the local top-k
-    if (A.precision == 0 || qC <= A.R) {
+    if (MET != 0 || A.precision == 0 || qC <= A.R) {  // the coarse passes serve the squared distance only
         if (A.ld / 4 >= 64 && A.ld / 4 < 128)
-            rerank_fp32<NT, S6_CH_LONG>(A, q4, slots, mine, keys);
+            rerank_fp32<NT, S6_CH_LONG, MET>(A, q4, slots, mine, keys);
         else
-            rerank_fp32<NT, S6_CH_SHORT>(A, q4, slots, mine, keys);
+            rerank_fp32<NT, S6_CH_SHORT, MET>(A, q4, slots, mine, keys);
         __syncthreads();
-    } else {
+    } else if constexpr (MET == 0) {
         // coarse pass on the reduced-precision copy, then the R smallest
         // coarse keys of the whole cluster survive into the exact pass
         if (A.precision == 1)
@@ -1780,9 +1776,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
         __syncthreads();
         nk = *ns;
         if (A.ld / 4 >= 64 && A.ld / 4 < 128)
-            rerank_fp32<NT, S6_CH_LONG>(A, q4, surv_ids, nk, keys);
+            rerank_fp32<NT, S6_CH_LONG, 0>(A, q4, surv_ids, nk, keys);
         else
-            rerank_fp32<NT, S6_CH_SHORT>(A, q4, surv_ids, nk, keys);
+            rerank_fp32<NT, S6_CH_SHORT, 0>(A, q4, surv_ids, nk, keys);
         __syncthreads();
     }
 
@@ -2097,10 +2093,10 @@ struct OccKey {
 std::mutex g_occ_mu;
 std::vector<std::pair<OccKey, int>> g_occ;
 
-template <int NT, int NSMAX>
+template <int NT, int NSMAX, int MET>
 int launch_t(const Layout& L, int64_t nq, bool persistent, uint32_t* work, cudaStream_t st)
 {
-    auto kern = suco_query_kernel<NT, NSMAX>;
+    auto kern = suco_query_kernel<NT, NSMAX, MET>;
     SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     if (L.A.CL > 8) SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg;
@@ -2145,21 +2141,29 @@ int launch_t(const Layout& L, int64_t nq, bool persistent, uint32_t* work, cudaS
     return SUCO_OK;
 }
 
-int dispatch(const Layout& L, int NT, int nsmax, int64_t nq, bool persistent, uint32_t* work, cudaStream_t st)
+// L1 indexes run 512-thread CTAs only (one more set of instantiations)
+int dispatch(const Layout& L, int NT, int nsmax, int metric, int64_t nq, bool persistent, uint32_t* work,
+             cudaStream_t st)
 {
+    if (metric == SUCO_METRIC_L1) {
+        if (NT != 512) return fail(SUCO_EUNSUPPORTED, "an L1 index runs CTAs of 512 threads (this launch needs %d)", NT);
+        if (nsmax == 8) return launch_t<512, 8, 1>(L, nq, persistent, work, st);
+        if (nsmax == 16) return launch_t<512, 16, 1>(L, nq, persistent, work, st);
+        return launch_t<512, 32, 1>(L, nq, persistent, work, st);
+    }
     if (NT == 1024) {
-        if (nsmax == 8) return launch_t<1024, 8>(L, nq, persistent, work, st);
-        if (nsmax == 16) return launch_t<1024, 16>(L, nq, persistent, work, st);
-        return launch_t<1024, 32>(L, nq, persistent, work, st);
+        if (nsmax == 8) return launch_t<1024, 8, 0>(L, nq, persistent, work, st);
+        if (nsmax == 16) return launch_t<1024, 16, 0>(L, nq, persistent, work, st);
+        return launch_t<1024, 32, 0>(L, nq, persistent, work, st);
     }
     if (NT == 256) {
-        if (nsmax == 8) return launch_t<256, 8>(L, nq, persistent, work, st);
-        if (nsmax == 16) return launch_t<256, 16>(L, nq, persistent, work, st);
-        return launch_t<256, 32>(L, nq, persistent, work, st);
+        if (nsmax == 8) return launch_t<256, 8, 0>(L, nq, persistent, work, st);
+        if (nsmax == 16) return launch_t<256, 16, 0>(L, nq, persistent, work, st);
+        return launch_t<256, 32, 0>(L, nq, persistent, work, st);
     }
-    if (nsmax == 8) return launch_t<512, 8>(L, nq, persistent, work, st);
-    if (nsmax == 16) return launch_t<512, 16>(L, nq, persistent, work, st);
-    return launch_t<512, 32>(L, nq, persistent, work, st);
+    if (nsmax == 8) return launch_t<512, 8, 0>(L, nq, persistent, work, st);
+    if (nsmax == 16) return launch_t<512, 16, 0>(L, nq, persistent, work, st);
+    return launch_t<512, 32, 0>(L, nq, persistent, work, st);
 }
 
 }  // namespace
@@ -2255,6 +2259,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     A.X8 = ix->X8;
     A.ld8 = ix->ld8;
     A.s8col = ix->s8col;
+    A.qperm = ix->dperm;
 
     if (dbg) {
         A.dbg_teff = dbg->t_eff;
@@ -2293,7 +2298,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
             if (base.dbg_clk) C2.dbg_clk = base.dbg_clk + c0 * 16 * NCLK;
             uint32_t* work = ix->work + (size_t)WORK_STRIDE * (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next,
                                                                                 1u, __ATOMIC_RELAXED) % WORK_SLOTS);
-            rc = dispatch(L, NT, nsmax, cnt, persistent, work, st);
+            rc = dispatch(L, NT, nsmax, ix->metric, cnt, persistent, work, st);
             if (rc) return rc;
         }
         return SUCO_OK;
@@ -2302,7 +2307,7 @@ int launch_query(const DeviceIndex* ix, const float* Q, int64_t nq, const suco_q
     uint32_t* work = ix->work + (size_t)WORK_STRIDE *
                                     (__atomic_fetch_add(&const_cast<DeviceIndex*>(ix)->work_next, 1u,
                                                         __ATOMIC_RELAXED) % WORK_SLOTS);
-    return dispatch(L, NT, nsmax, nq, persistent, work, st);
+    return dispatch(L, NT, nsmax, ix->metric, nq, persistent, work, st);
 }
 
 }  // namespace suco

@@ -77,10 +77,13 @@ __device__ __forceinline__ uint32_t e4m3_code(float x, float scale, float* value
 // one row of a K-major operand: 16 bytes per core-matrix column (8 BF16 or
 // 16 E4M3 values), each a 16-byte store; returns the row's squared norm (FP32,
 // element order) of the values the codes stand for
+// src[k] of the row is base[idx ? idx[off + k] : off + k] (idx: a sampled
+// index's column permutation, for query rows)
 template <bool FP8>
-__device__ __forceinline__ float stage_row(const float* __restrict__ src, int len, bool valid, float scale, int kcols,
-                                           char* row_base)
+__device__ __forceinline__ float stage_row(const float* __restrict__ base, const int32_t* __restrict__ idx, int off,
+                                           int len, bool valid, float scale, int kcols, char* row_base)
 {
+    auto src = [&](int k) { return base[idx ? __ldg(idx + off + k) : off + k]; };
     float nrm = 0.f;
     for (int kc = 0; kc < kcols; ++kc) {
         uint32_t w[4] = {0u, 0u, 0u, 0u};
@@ -89,7 +92,7 @@ __device__ __forceinline__ float stage_row(const float* __restrict__ src, int le
             for (int e = 0; e < 16; ++e) {
                 const int k = kc * 16 + e;
                 float v = 0.f;
-                const uint32_t code = (valid && k < len) ? e4m3_code(src[k], scale, &v) : 0u;
+                const uint32_t code = (valid && k < len) ? e4m3_code(src(k), scale, &v) : 0u;
                 nrm = __fmaf_rn(v, v, nrm);
                 w[e >> 2] |= code << (8 * (e & 3));
             }
@@ -97,8 +100,8 @@ __device__ __forceinline__ float stage_row(const float* __restrict__ src, int le
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {
                 const int k = kc * 8 + e;
-                const float x0 = (valid && k < len) ? src[k] : 0.f;
-                const float x1 = (valid && k + 1 < len) ? src[k + 1] : 0.f;
+                const float x0 = (valid && k < len) ? src(k) : 0.f;
+                const float x1 = (valid && k + 1 < len) ? src(k + 1) : 0.f;
                 const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
                 const float r0 = __bfloat162float(h0), r1 = __bfloat162float(h1);
                 nrm = __fmaf_rn(r0, r0, nrm);
@@ -151,8 +154,8 @@ template <bool FP8>
 __global__ void __launch_bounds__(128, 1)
     centroid_dist_tc_kernel(const float* __restrict__ Q, int64_t nq, int32_t d, int32_t Ns, int32_t sub_s,
                             int32_t sqrtK, int32_t hmax, const float* __restrict__ cent,
-                            const float* __restrict__ col_scale, int32_t KP, int32_t NP, int32_t ncols,
-                            float* __restrict__ D, uint32_t* status)
+                            const float* __restrict__ col_scale, const int32_t* __restrict__ qperm, int32_t KP,
+                            int32_t NP, int32_t ncols, float* __restrict__ D, uint32_t* status)
 {
     extern __shared__ __align__(128) char smem[];
     constexpr int ESZ = FP8 ? 1 : 2;  // bytes per element
@@ -186,16 +189,16 @@ __global__ void __launch_bounds__(128, 1)
     float t = 1.f;  // the query's scale over subspace i (FP8)
     if (FP8 && b < nq) {
         float mx = 0.f;
-        for (int j = 0; j < slen; ++j) mx = fmaxf(mx, fabsf(Q[b * d + soff + j]));
+        for (int j = 0; j < slen; ++j) mx = fmaxf(mx, fabsf(query_col(Q + b * d, qperm, soff + j)));
         t = mx > 0.f ? __fdiv_rn(mx, 448.f) : 1.f;
     }
-    const float qn = stage_row<FP8>(Q + (b < nq ? b : 0) * d + off, len, b < nq, t, kcols,
+    const float qn = stage_row<FP8>(Q + (b < nq ? b : 0) * d, qperm, off, len, b < nq, t, kcols,
                                     As + ((m >> 3) * kcols) * 128 + (m & 7) * 16);
     // B: centroid c of this half, same layout with c in place of m
     const float s = FP8 ? col_scale[soff] : 1.f;
     for (int c = tid; c < NP; c += TC_M)
-        cn[c] = stage_row<FP8>(cent + ((int64_t)ih * sqrtK + (c < sqrtK ? c : 0)) * hmax, len, c < sqrtK, s, kcols,
-                               Bs + ((c >> 3) * kcols) * 128 + (c & 7) * 16);
+        cn[c] = stage_row<FP8>(cent + ((int64_t)ih * sqrtK + (c < sqrtK ? c : 0)) * hmax, nullptr, 0, len, c < sqrtK, s,
+                               kcols, Bs + ((c >> 3) * kcols) * 128 + (c & 7) * 16);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -292,7 +295,8 @@ int rank_tc_tables(const DeviceIndex* ix, const float* Q, int64_t nq, float* D, 
     SUCO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req));
     const int64_t tiles = (nq + TC_M - 1) / TC_M;
     kern<<<dim3((unsigned)tiles, (unsigned)(2 * ix->Ns)), TC_M, smem_req, st>>>(
-        Q, nq, ix->d, ix->Ns, ix->sub_s, ix->sqrtK, ix->hmax, ix->cent, ix->s8col, KP, NP, ncols, D, ix->status_dev);
+        Q, nq, ix->d, ix->Ns, ix->sub_s, ix->sqrtK, ix->hmax, ix->cent, ix->s8col, ix->dperm, KP, NP, ncols, D,
+        ix->status_dev);
     SUCO_LAUNCH_CHECK("centroid_dist_tc_kernel");
     return SUCO_OK;
 }

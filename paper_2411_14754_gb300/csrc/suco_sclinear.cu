@@ -6,9 +6,11 @@
 //
 // A batch of B queries runs as a pipeline of launches over a caller-provided
 // workspace:
-//   1. scl_dist_kernel    FP32 squared distance of every point to every query
-//                         in every subspace (x_j - q_j, one fused multiply-add
-//                         per dimension, in dimension order), stored [B][Ns][n];
+//   1. scl_dist_kernel    FP32 distance of every point to every query in every
+//                         subspace (x_j - q_j, one fused multiply-add per
+//                         dimension for the squared Euclidean distance, one
+//                         addition of |x_j - q_j| for L1, in dimension order),
+//                         stored [B][Ns][n];
 //   2. scl_select_kernel  per (query, subspace), the exact T-th smallest key
 //                         (distance bits, id): a radix select over the
 //                         distance bits (11/11/10-bit digits, warp-aggregated
@@ -78,7 +80,8 @@ SclLayout scl_layout(const DeviceIndex* ix, int64_t B, int64_t C)
 // and every thread keeps one accumulator per query.
 __global__ void __launch_bounds__(256) scl_dist_kernel(const float* __restrict__ X, int64_t ld, int64_t n, int32_t d,
                                                        int32_t Ns, int32_t sub_s, const float* __restrict__ Q, int64_t nq,
-                                                       float* __restrict__ dist)
+                                                       float* __restrict__ dist, const int32_t* __restrict__ qperm,
+                                                       int metric)
 {
     extern __shared__ float qs[];  // [SCL_QT][slen]
     const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(256) scl_dist_kernel(const float* __restrict__
         __syncthreads();
         for (int t = threadIdx.x; t < nqg * len; t += 256) {
             const int qq = t / len, j = t - qq * len;
-            qs[t] = Q[(q0 + qq) * d + off + j];
+            qs[t] = query_col(Q + (q0 + qq) * d, qperm, off + j);
         }
         __syncthreads();
         if (p >= n) continue;
@@ -109,7 +112,8 @@ __global__ void __launch_bounds__(256) scl_dist_kernel(const float* __restrict__
                     for (int u = 0; u < SCL_DC; ++u)
                         if (j0 + u < len) {
                             const float df = __fsub_rn(xv[u], qv[u]);
-                            acc[qq] = __fmaf_rn(df, df, acc[qq]);
+                            acc[qq] = metric == SUCO_METRIC_L1 ? __fadd_rn(acc[qq], fabsf(df))
+                                                               : __fmaf_rn(df, df, acc[qq]);
                         }
                 }
             }
@@ -421,7 +425,8 @@ constexpr int RR_NT = 512;
 __global__ void __launch_bounds__(RR_NT) scl_rerank_kernel(const float* __restrict__ X, int64_t ld, const float* __restrict__ Q,
                                                            int32_t d, const int32_t* __restrict__ cands, int64_t C,
                                                            int32_t k, unsigned long long* __restrict__ keys,
-                                                           int32_t* __restrict__ out_ids, float* __restrict__ out_dist)
+                                                           int32_t* __restrict__ out_ids, float* __restrict__ out_dist,
+                                                           const int32_t* __restrict__ qperm, int metric)
 {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t wtmp[RR_NT / 32 + 4];
@@ -432,10 +437,10 @@ __global__ void __launch_bounds__(RR_NT) scl_rerank_kernel(const float* __restri
     const int ld4 = (int)(ld / 4);
     for (int c = threadIdx.x; c < ld4; c += RR_NT) {
         float4 v;
-        v.x = 4 * c + 0 < d ? Q[b * d + 4 * c + 0] : 0.f;
-        v.y = 4 * c + 1 < d ? Q[b * d + 4 * c + 1] : 0.f;
-        v.z = 4 * c + 2 < d ? Q[b * d + 4 * c + 2] : 0.f;
-        v.w = 4 * c + 3 < d ? Q[b * d + 4 * c + 3] : 0.f;
+        v.x = 4 * c + 0 < d ? query_col(Q + b * d, qperm, 4 * c + 0) : 0.f;
+        v.y = 4 * c + 1 < d ? query_col(Q + b * d, qperm, 4 * c + 1) : 0.f;
+        v.z = 4 * c + 2 < d ? query_col(Q + b * d, qperm, 4 * c + 2) : 0.f;
+        v.w = 4 * c + 3 < d ? query_col(Q + b * d, qperm, 4 * c + 3) : 0.f;
         qsm[c] = v;
     }
     __syncthreads();
@@ -449,14 +454,10 @@ __global__ void __launch_bounds__(RR_NT) scl_rerank_kernel(const float* __restri
         if (r < C)
             for (int c = gl; c < ld4; c += 8) {
                 const float4 x = __ldg(X4 + (int64_t)id * ld4 + c), q = qsm[c];
-                float df = __fsub_rn(x.x, q.x);
-                acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(x.y, q.y);
-                acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(x.z, q.z);
-                acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(x.w, q.w);
-                acc = __fmaf_rn(df, df, acc);
+                const float df[4] = {__fsub_rn(x.x, q.x), __fsub_rn(x.y, q.y), __fsub_rn(x.z, q.z), __fsub_rn(x.w, q.w)};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    acc = metric == SUCO_METRIC_L1 ? __fadd_rn(acc, fabsf(df[e])) : __fmaf_rn(df[e], df[e], acc);
             }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
@@ -528,7 +529,7 @@ int sc_linear_chunk(const DeviceIndex* ix, const float* Q, int64_t bq, uint32_t 
     if (dsmem > 48 * 1024)
         SUCO_CUDA_TRY(cudaFuncSetAttribute(scl_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
     scl_dist_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)((bq + SCL_QT - 1) / SCL_QT)), 256, dsmem, st>>>(
-        ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, Q, bq, dist);
+        ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, Q, bq, dist, ix->dperm, ix->metric);
     SUCO_LAUNCH_CHECK("scl_dist_kernel");
     scl_select_kernel<<<(unsigned)(bq * Ns), SEL_NT, 0, st>>>(dist, n, T, kappa);
     SUCO_LAUNCH_CHECK("scl_select_kernel");
@@ -545,7 +546,7 @@ int sc_linear_chunk(const DeviceIndex* ix, const float* Q, int64_t bq, uint32_t 
     scl_compact_kernel<<<dim3((unsigned)ntile, (unsigned)bq), 256, 0, st>>>(score, n, cut, tcnt, C, cands);
     SUCO_LAUNCH_CHECK("scl_compact_kernel");
     scl_rerank_kernel<<<(unsigned)bq, RR_NT, (size_t)ix->ld * 4, st>>>(ix->X, ix->ld, Q, ix->d, cands, C, k, keys,
-                                                                       ids, dist_out);
+                                                                       ids, dist_out, ix->dperm, ix->metric);
     SUCO_LAUNCH_CHECK("scl_rerank_kernel");
     if (dbg_scores)
         SUCO_CUDA_TRY(cudaMemcpyAsync(dbg_scores, score, (size_t)bq * n, cudaMemcpyDeviceToDevice, st));

@@ -23,8 +23,8 @@ class SucoError(RuntimeError):
 
 
 class _BuildParams(C.Structure):
-    _fields_ = [("Ns", C.c_int32), ("sqrtK", C.c_int32), ("kmeans_iters", C.c_int32), ("reserved0", C.c_int32),
-                ("seed", C.c_uint64), ("init_ids", C.c_void_p)]
+    _fields_ = [("Ns", C.c_int32), ("sqrtK", C.c_int32), ("kmeans_iters", C.c_int32), ("metric", C.c_int32),
+                ("seed", C.c_uint64), ("init_ids", C.c_void_p), ("dim_perm", C.c_void_p)]
 
 
 class _QueryParams(C.Structure):
@@ -50,7 +50,8 @@ class SucoMlp(C.Structure):
 
 class _IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("Ns", C.c_int32), ("sqrtK", C.c_int32), ("hmax", C.c_int32),
-                ("K", C.c_int64), ("ld", C.c_int64), ("device_bytes", C.c_int64)]
+                ("K", C.c_int64), ("ld", C.c_int64), ("device_bytes", C.c_int64), ("metric", C.c_int32),
+                ("sampled", C.c_int32)]
 
 
 def library_path() -> str:
@@ -70,6 +71,7 @@ def load_library():
     vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     L.suco_build_index.argtypes = [vp, i64, i32, C.POINTER(_BuildParams), vp, C.POINTER(vp)]
     L.suco_build_index_from_assignments.argtypes = [vp, i64, i32, i32, i32, vp, vp, vp, C.POINTER(vp)]
+    L.suco_build_index_from_parts.argtypes = [vp, i64, i32, C.POINTER(_BuildParams), vp, vp, vp, C.POINTER(vp)]
     L.suco_query_batch.argtypes = [vp, vp, i64, C.POINTER(_QueryParams), vp, vp, vp]
     L.suco_query_debug.argtypes = [vp, vp, i64, C.POINTER(_QueryParams), vp, vp, C.POINTER(_DebugOut), vp]
     L.suco_index_get_info.argtypes = [vp, C.POINTER(_IndexInfo)]
@@ -91,7 +93,8 @@ def load_library():
     L.suco_free.argtypes = [vp]
     L.suco_free.restype = None
     L.suco_last_error.restype = C.c_char_p
-    for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_query_batch", "suco_query_debug",
+    for name in ("suco_build_index", "suco_build_index_from_assignments", "suco_build_index_from_parts",
+                 "suco_query_batch", "suco_query_debug",
                  "suco_index_get_info", "suco_export_index", "suco_thresholds", "suco_version",
                  "suco_kmeans_noalloc", "suco_autotune", "suco_query_features", "suco_mlp_predict",
                  "suco_mlp_forward", "suco_mlp_backward", "suco_adamw_step", "suco_add_reduced_copies", "suco_read_status",
@@ -148,6 +151,7 @@ class SucoIndex:
         _check(load_library().suco_index_get_info(handle, C.byref(info)))
         self.n, self.d, self.Ns, self.sqrtK = info.n, info.d, info.Ns, info.sqrtK
         self.hmax, self.K, self.ld, self.device_bytes = info.hmax, info.K, info.ld, info.device_bytes
+        self.metric, self.sampled = info.metric, info.sampled
 
     def __enter__(self):
         return self
@@ -162,12 +166,23 @@ class SucoIndex:
             pass
 
 
+METRIC = {"l2": 0, "l1": 1}
+
+
+def _perm_arg(dim_perm):
+    return None if dim_perm is None else np.ascontiguousarray(dim_perm, dtype=np.int32)
+
+
 def suco_build_index(data: torch.Tensor, Ns: int, sqrtK: int, kmeans_iters: int = 20, seed: int = 0,
-                     init_ids: Optional[np.ndarray] = None, stream=None) -> SucoIndex:
-    """Algorithm 2 on the GPU.  ``data``: n x d float32 CUDA tensor (copied)."""
+                     init_ids: Optional[np.ndarray] = None, stream=None, metric="l2", dim_perm=None) -> SucoIndex:
+    """Algorithm 2 on the GPU.  ``data``: n x d float32 CUDA tensor (copied).
+    metric "l2" (squared Euclidean) or "l1"; dim_perm: Definition 3's subspace
+    sampling as a permutation of the d dims (None: contiguous subspaces)."""
     _dev_f32(data, "data")
     ids = None if init_ids is None else np.ascontiguousarray(init_ids, dtype=np.int64)
-    p = _BuildParams(Ns, sqrtK, kmeans_iters, 0, seed, None if ids is None else ids.ctypes.data)
+    pm = _perm_arg(dim_perm)
+    p = _BuildParams(Ns, sqrtK, kmeans_iters, METRIC[metric] if isinstance(metric, str) else int(metric), seed,
+                     None if ids is None else ids.ctypes.data, None if pm is None else pm.ctypes.data)
     h = C.c_void_p()
     _check(load_library().suco_build_index(_ptr(data), data.shape[0], data.shape[1], C.byref(p), _stream(stream),
                                            C.byref(h)))
@@ -184,6 +199,23 @@ def suco_build_index_from_assignments(data: torch.Tensor, Ns: int, sqrtK: int, c
     _check(load_library().suco_build_index_from_assignments(_ptr(data), data.shape[0], data.shape[1], Ns, sqrtK,
                                                             cent.ctypes.data, asg.ctypes.data, _stream(stream),
                                                             C.byref(h)))
+    return SucoIndex(h)
+
+
+def suco_build_index_from_parts(data: torch.Tensor, Ns: int, sqrtK: int, centroids, assign, metric="l2",
+                                dim_perm=None, stream=None) -> SucoIndex:
+    """The IMI from given centroids [Ns][2][sqrtK][hmax] (over each half's dims
+    in the sampling's order) and assignments [Ns][2][n], for any metric and
+    subspace sampling."""
+    _dev_f32(data, "data")
+    cent = np.ascontiguousarray(centroids, dtype=np.float32)
+    asg = np.ascontiguousarray(assign, dtype=np.int32)
+    pm = _perm_arg(dim_perm)
+    p = _BuildParams(Ns, sqrtK, 0, METRIC[metric] if isinstance(metric, str) else int(metric), 0, None,
+                     None if pm is None else pm.ctypes.data)
+    h = C.c_void_p()
+    _check(load_library().suco_build_index_from_parts(_ptr(data), data.shape[0], data.shape[1], C.byref(p),
+                                                      cent.ctypes.data, asg.ctypes.data, _stream(stream), C.byref(h)))
     return SucoIndex(h)
 
 

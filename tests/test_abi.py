@@ -113,12 +113,13 @@ def test_fault_injection_on_the_host_without_a_gpu(lib):
 
     class Params(ctypes.Structure):
         _fields_ = [("Ns", ctypes.c_int32), ("sqrtK", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32),
-                    ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64), ("init_ids", ctypes.c_void_p)]
+                    ("metric", ctypes.c_int32), ("seed", ctypes.c_uint64), ("init_ids", ctypes.c_void_p),
+                    ("dim_perm", ctypes.c_void_p)]
 
     lib.suco_build_index.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Params),
                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
     out = ctypes.c_void_p()
-    p = Params(2, 4, 1, 0, 7, None)
+    p = Params(2, 4, 1, 0, 7, None, None)
     assert lib.suco_inject_fault(1, 0) == 0                       # SUCO_FAULT_ALLOC, the next allocation
     rc = lib.suco_build_index(ctypes.c_void_p(16), 100, 8, ctypes.byref(p), None, ctypes.byref(out))
     assert rc == -2 and out.value is None
