@@ -38,18 +38,21 @@ __global__ void init_centroids_kernel(const float* __restrict__ X, int64_t ld, i
     }
 }
 
-// Largest |x| of each half-subspace, as float bits (monotone for x >= 0).
+// Largest |x| of each of the first H half-subspaces, as float bits
+// (monotone for x >= 0).  Thread c of a block reads column c of the block's
+// rows, so a warp reads consecutive columns of one row (coalesced).
 __global__ void maxabs_kernel(const float* __restrict__ X, int64_t ld, int64_t n, int32_t d, int32_t Ns, int32_t sub_s,
-                              unsigned* __restrict__ out)
+                              int32_t H, unsigned* __restrict__ out)
 {
-    const int ih = blockIdx.y;
-    int32_t off, len;
-    half_dims(d, Ns, sub_s, ih >> 1, ih & 1, &off, &len);
-    float m = 0.f;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
-        for (int j = 0; j < len; ++j) m = fmaxf(m, fabsf(X[p * ld + off + j]));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out + ih, __float_as_uint(m));
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        const int i = min(c / sub_s, Ns - 1);
+        const int slen = (i == Ns - 1) ? d - (Ns - 1) * sub_s : sub_s;
+        const int ih = 2 * i + ((c - i * sub_s) >= slen / 2 ? 1 : 0);
+        if (ih >= H) continue;
+        float m = 0.f;
+        for (int64_t p = blockIdx.x; p < n; p += gridDim.x) m = fmaxf(m, fabsf(X[p * ld + c]));
+        atomicMax(out + ih, __float_as_uint(m));
+    }
 }
 
 // One dimension's term of the index's distance, accumulated in FP32:
@@ -60,12 +63,16 @@ __device__ __forceinline__ float dist_term(float acc, float df, int metric)
 }
 
 // Nearest centroid of every point in one half-subspace (grid.y = half), in
-// the index's metric.
+// the index's metric.  Each block stages the half's centroids and then, tile
+// by tile, its points' half-slices in shared memory with coalesced loads
+// (row stride len | 1, so the threads' reads fall in distinct banks); each
+// thread then scans the centroids for its point, dims in order.
+// Shared memory: sqrtK*len + blockDim.x*(len|1) floats.
 __global__ void kmeans_assign_kernel(const float* __restrict__ X, int64_t ld, int64_t n, int32_t d, int32_t Ns,
                                      int32_t sub_s, int32_t sqrtK, int32_t hmax, const float* __restrict__ cent,
                                      int32_t* __restrict__ assign, int metric)
 {
-    extern __shared__ float s_cent[];  // sqrtK * len
+    extern __shared__ float s_cent[];  // sqrtK * len, then the tile
     const int ih = blockIdx.y;
     int32_t off, len;
     half_dims(d, Ns, sub_s, ih >> 1, ih & 1, &off, &len);
@@ -74,15 +81,26 @@ __global__ void kmeans_assign_kernel(const float* __restrict__ X, int64_t ld, in
         const int a = t / len, j = t - a * len;
         s_cent[t] = cb[a * hmax + j];
     }
-    __syncthreads();
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const float* x = X + p * ld + off;
+    float* s_x = s_cent + sqrtK * len;
+    const int xs = len | 1;
+    const int TP = blockDim.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * TP; p0 < n; p0 += (int64_t)gridDim.x * TP) {  // block-uniform
+        __syncthreads();
+        for (int t = threadIdx.x; t < TP * len; t += TP) {
+            const int pp = t / len, j = t - pp * len;
+            const int64_t p = p0 + pp;
+            s_x[pp * xs + j] = p < n ? X[p * ld + off + j] : 0.f;
+        }
+        __syncthreads();
+        const int64_t p = p0 + threadIdx.x;
+        if (p >= n) continue;
+        const float* x = s_x + threadIdx.x * xs;
         int best = 0;
         float bd = INFINITY;
         if (len <= 32) {
             float xr[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) xr[j] = (j < len) ? __ldg(x + j) : 0.f;
+            for (int j = 0; j < 32; ++j) xr[j] = (j < len) ? x[j] : 0.f;
             for (int a = 0; a < sqrtK; ++a) {
                 const float* c = s_cent + a * len;
                 float acc = 0.f;
@@ -98,7 +116,7 @@ __global__ void kmeans_assign_kernel(const float* __restrict__ X, int64_t ld, in
             for (int a = 0; a < sqrtK; ++a) {
                 const float* c = s_cent + a * len;
                 float acc = 0.f;
-                for (int j = 0; j < len; ++j) acc = dist_term(acc, __fsub_rn(__ldg(x + j), c[j]), metric);
+                for (int j = 0; j < len; ++j) acc = dist_term(acc, __fsub_rn(x[j], c[j]), metric);
                 if (acc < bd) {
                     bd = acc;
                     best = a;
@@ -227,6 +245,22 @@ cudaError_t raise_smem_limit(K* kern, size_t bytes)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Points per block of the assignment kernel (256, 128 or 64: the largest
+// whose centroid table and point slices fit the opt-in shared memory) and its
+// dynamic shared memory; false if not even 64 fit.
+bool assign_shape(int k, int len, int optin, int* tp, size_t* smem)
+{
+    for (int t = 256; t >= 64; t /= 2) {
+        const size_t b = ((size_t)k * len + (size_t)t * (len | 1)) * 4;
+        if (b <= (size_t)optin) {
+            *tp = t;
+            *smem = b;
+            return true;
+        }
+    }
+    return false;
+}
+
 int grid_for(int64_t work, int threads, int cap = 65535)
 {
     int64_t g = (work + threads - 1) / threads;
@@ -283,8 +317,8 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
 
     // fixed-point scale per half: max|x| * 2^S * n < 2^62
     SUCO_CUDA_TRY(cudaMemsetAsync(maxabs.p, 0, (size_t)H * 4, st));
-    maxabs_kernel<<<dim3(grid_for(n, 256, 1024), H), 256, 0, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s,
-                                                                   maxabs.as<unsigned>());
+    maxabs_kernel<<<grid_for(n, 1, 8 * 152), 256, 0, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, H,
+                                                            maxabs.as<unsigned>());
     SUCO_LAUNCH_CHECK("maxabs_kernel");
     std::vector<unsigned> mbits(H);
     SUCO_CUDA_TRY(cudaMemcpyAsync(mbits.data(), maxabs.p, (size_t)H * 4, cudaMemcpyDeviceToHost, st));
@@ -314,19 +348,20 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
     }
     int dev_smem_optin = 0;
     SUCO_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
-    const size_t assign_smem = (size_t)sk * max_len * 4;
+    int atp = 0;
+    size_t assign_smem = 0;
     const size_t accum_smem = (size_t)sk * max_len * 8 + (size_t)sk * 4;
-    if (assign_smem > (size_t)dev_smem_optin)
-        return fail(SUCO_EUNSUPPORTED, "centroid table of %zu bytes exceeds shared memory", assign_smem);
+    if (!assign_shape(sk, max_len, dev_smem_optin, &atp, &assign_smem))
+        return fail(SUCO_EUNSUPPORTED, "centroid table of %zu bytes exceeds shared memory", (size_t)sk * max_len * 4);
     const int use_smem = accum_smem <= (size_t)dev_smem_optin ? 1 : 0;
     SUCO_CUDA_TRY(raise_smem_limit(kmeans_assign_kernel, assign_smem));
     if (use_smem) SUCO_CUDA_TRY(raise_smem_limit(kmeans_accum_kernel, accum_smem));
     int nsm = 0;
     SUCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ix->device));
-    const dim3 g_assign(grid_for(n, 256, 8 * nsm), H);
+    const dim3 g_assign(grid_for(n, atp, 8 * nsm), H);
     const dim3 g_accum(grid_for(n, 256, 2 * nsm), H);
     for (int it = 0; it < iters; ++it) {
-        kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm,
+        kmeans_assign_kernel<<<g_assign, atp, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm,
                                                                 ix->cent, assign.as<int32_t>(), ix->metric);
         SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
         SUCO_CUDA_TRY(cudaMemsetAsync(gsum.p, 0, gsum.bytes, st));
@@ -341,7 +376,7 @@ int kmeans_build(DeviceIndex* ix, const int64_t* init_ids_host, int32_t iters, c
         SUCO_LAUNCH_CHECK("kmeans_finalize_kernel");
     }
     // the assignment that defines the IMI, against the final centroids
-    kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm, ix->cent,
+    kmeans_assign_kernel<<<g_assign, atp, assign_smem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, sk, hm, ix->cent,
                                                             assign.as<int32_t>(), ix->metric);
     SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
     return build_imi(ix, assign.as<int32_t>(), st);
@@ -428,7 +463,7 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
 
     // fixed-point scale: max|x| * 2^S * n < 2^62
     SUCO_CUDA_TRY(cudaMemsetAsync(maxabs, 0, 4, st));
-    maxabs_kernel<<<dim3(grid_for(n, 256, 1024), 1), 256, 0, st>>>(Xc, d, n, dd, 1, sub, maxabs);
+    maxabs_kernel<<<grid_for(n, 1, 8 * 152), 256, 0, st>>>(Xc, d, n, dd, 1, sub, 1, maxabs);
     SUCO_LAUNCH_CHECK("maxabs_kernel");
     unsigned mbits = 0;
     SUCO_CUDA_TRY(cudaMemcpyAsync(&mbits, maxabs, 4, cudaMemcpyDeviceToHost, st));
@@ -445,16 +480,19 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
     const float sc[2] = {std::ldexp(1.0f, S), std::ldexp(1.0f, -S)};
     SUCO_CUDA_TRY(cudaMemcpyAsync(scale, sc, 8, cudaMemcpyHostToDevice, st));
 
-    const size_t assign_smem = (size_t)k * dim_len * 4;
+    int atp = 0;
+    size_t assign_smem = 0;
+    if (!assign_shape(k, dim_len, smem_optin, &atp, &assign_smem))
+        return fail(SUCO_EUNSUPPORTED, "k=%d x dim_len=%d centroids exceed shared memory", k, dim_len);
     const size_t accum_smem = (size_t)k * dim_len * 8 + (size_t)k * 4;
     const int use_smem = accum_smem <= (size_t)smem_optin ? 1 : 0;
     // raise (never lower) the dynamic shared-memory limits of the shared kernels
     SUCO_CUDA_TRY(raise_smem_limit(kmeans_assign_kernel, assign_smem));
     if (use_smem) SUCO_CUDA_TRY(raise_smem_limit(kmeans_accum_kernel, accum_smem));
-    const dim3 g_assign(grid_for(n, 256, 8 * nsm), 1);
+    const dim3 g_assign(grid_for(n, atp, 8 * nsm), 1);
     const dim3 g_accum(grid_for(n, 256, 2 * nsm), 1);
     for (int it = 0; it < iters; ++it) {
-        kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign,
+        kmeans_assign_kernel<<<g_assign, atp, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign,
                                                                 SUCO_METRIC_L2);
         SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
         // sums and counts start from zero in every iteration (the array keeps the last call's contents)
@@ -468,7 +506,7 @@ extern "C" int suco_kmeans_noalloc(const float* data, int64_t n, int32_t d, int3
         SUCO_LAUNCH_CHECK("kmeans_finalize_kernel");
     }
     // the assignment against the final centroids
-    kmeans_assign_kernel<<<g_assign, 256, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign,
+    kmeans_assign_kernel<<<g_assign, atp, assign_smem, st>>>(Xc, d, n, dd, 1, sub, k, dim_len, centroids, assign,
                                                             SUCO_METRIC_L2);
     SUCO_LAUNCH_CHECK("kmeans_assign_kernel");
     return SUCO_OK;

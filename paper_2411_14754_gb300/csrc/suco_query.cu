@@ -1683,6 +1683,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) suco_
                 }
                 uint32_t pg = pgb + ig - cg, pe = peb + ie - ce;
                 const uint32_t base_id = id0 + g * 32;
+                // only the lowest-id ties at theta up to need_eq are taken:
+                // keep just this lane's share of them (the first need_eq - pe
+                // of its tie bits); the positions of the ids above theta count
+                // the ties before them capped at need_eq, so they are unchanged
+                {
+                    const uint32_t room = pe < need_eq ? need_eq - pe : 0u;
+                    if (room < ce) {
+                        uint32_t drop = em;
+                        for (uint32_t t = 0; t < room; ++t) drop &= drop - 1u;  // clear the lowest `room` set bits
+                        em &= ~drop;
+                    }
+                }
                 while (gm | em) {
                     const int j = __ffs(gm | em) - 1;
                     const uint32_t bit = 1u << j;
