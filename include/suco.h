@@ -339,8 +339,8 @@ SUCO_API int suco_sc_linear_workspace_size(const suco_index* index, int64_t batc
  *              nullable) [nq][C] candidate ids (the ids above the cut score
  *              first, in id order, then the ties at the cut in id order).
  * Asynchronous on `stream`; allocates nothing.
- * Errors: SUCO_EINVAL, SUCO_EUNSUPPORTED (Ns >= 64, or a subspace longer than
- * 1600 dims), SUCO_ECUDA. */
+ * Errors: SUCO_EINVAL, SUCO_EUNSUPPORTED (Ns >= 64, a subspace longer than
+ * 1600 dims, or d above 51200), SUCO_ECUDA. */
 SUCO_API int suco_sc_linear(const suco_index* index, const float* queries, int64_t nq, int32_t k, double alpha,
                             double beta, void* workspace, size_t workspace_bytes, int32_t* out_ids, float* out_dist,
                             uint8_t* dbg_scores, int32_t* dbg_cands, void* stream);

@@ -55,8 +55,8 @@ SclLayout scl_layout(const DeviceIndex* ix, int64_t B, int64_t C)
     L.B = B;
     const int64_t n = ix->n, ntile = (n + SCL_TILE - 1) / SCL_TILE;
     size_t o = 0;
-    L.o_dist = o;
-    o = align256(o + (size_t)B * ix->Ns * n * 4);
+    L.o_dist = o;  // rows of ldn = n rounded up to 4 floats: 16-byte aligned
+    o = align256(o + (size_t)B * ix->Ns * ((n + 3) & ~int64_t(3)) * 4);
     L.o_kappa = o;
     o = align256(o + (size_t)B * ix->Ns * 8);
     L.o_score = o;
@@ -78,21 +78,22 @@ SclLayout scl_layout(const DeviceIndex* ix, int64_t B, int64_t C)
 // 1. distances.  Block: 256 points x SCL_QT queries (grid.y picks the query
 // group); per subspace the group's query slices are staged in shared memory
 // and every thread keeps one accumulator per query.
-__global__ void __launch_bounds__(256) scl_dist_kernel(const float* __restrict__ X, int64_t ld, int64_t n, int32_t d,
+__global__ void __launch_bounds__(256, 2) scl_dist_kernel(const float* __restrict__ X, int64_t ld, int64_t n, int32_t d,
                                                        int32_t Ns, int32_t sub_s, const float* __restrict__ Q, int64_t nq,
-                                                       float* __restrict__ dist, const int32_t* __restrict__ qperm,
-                                                       int metric)
+                                                       float* __restrict__ dist, int64_t ldn,
+                                                       const int32_t* __restrict__ qperm, int metric)
 {
-    extern __shared__ float qs[];  // [SCL_QT][slen]
+    extern __shared__ __align__(16) float qs[];  // [SCL_QT][lq]: rows padded to 4 floats (16-byte loads)
     const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int64_t q0 = (int64_t)blockIdx.y * SCL_QT;
     const int nqg = (int)(nq - q0 < SCL_QT ? nq - q0 : SCL_QT);
     for (int i = 0; i < Ns; ++i) {
         const int off = i * sub_s, len = (i == Ns - 1) ? d - (Ns - 1) * sub_s : sub_s;
+        const int lq = (len + 3) & ~3;
         __syncthreads();
         for (int t = threadIdx.x; t < nqg * len; t += 256) {
             const int qq = t / len, j = t - qq * len;
-            qs[t] = query_col(Q + (q0 + qq) * d, qperm, off + j);
+            qs[qq * lq + j] = query_col(Q + (q0 + qq) * d, qperm, off + j);
         }
         __syncthreads();
         if (p >= n) continue;
@@ -107,7 +108,9 @@ __global__ void __launch_bounds__(256) scl_dist_kernel(const float* __restrict__
 #pragma unroll
             for (int qq = 0; qq < SCL_QT; ++qq) {
                 if (qq < nqg) {
-                    const float* qv = qs + qq * len + j0;
+                    const float4 qa = *reinterpret_cast<const float4*>(qs + qq * lq + j0);  // j0 % 8 == 0
+                    const float4 qb = j0 + 4 < lq ? *reinterpret_cast<const float4*>(qs + qq * lq + j0 + 4) : qa;
+                    const float qv[SCL_DC] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
 #pragma unroll
                     for (int u = 0; u < SCL_DC; ++u)
                         if (j0 + u < len) {
@@ -120,8 +123,39 @@ __global__ void __launch_bounds__(256) scl_dist_kernel(const float* __restrict__
         }
 #pragma unroll
         for (int qq = 0; qq < SCL_QT; ++qq)
-            if (qq < nqg) dist[((q0 + qq) * Ns + i) * n + p] = acc[qq];
+            if (qq < nqg) dist[((q0 + qq) * Ns + i) * ldn + p] = acc[qq];
     }
+}
+
+// Exclusive sum over the 1024 threads of a block (wtmp: 33 words); *tot gets
+// the total.  Ends with a barrier, so wtmp can be reused at once.
+__device__ __forceinline__ uint32_t block_scan_pairs_1024(uint32_t v, uint32_t* wtmp, uint32_t* tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtmp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t t = wtmp[lane];
+        uint32_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        wtmp[lane] = ti - t;
+        if (lane == 31) wtmp[32] = ti;
+    }
+    __syncthreads();
+    const uint32_t r = wtmp[w] + incl - v;
+    *tot = wtmp[32];
+    __syncthreads();
+    return r;
 }
 
 // Adds 1 to hist[bin] for every lane with `valid`, one atomic per distinct
@@ -195,12 +229,13 @@ __device__ uint32_t block_find_bin(const uint32_t* hist, int nb, uint32_t need, 
 // collides iff dist < d*, or dist == d* and id <= last id.
 constexpr int SEL_NT = 1024;
 
-__global__ void __launch_bounds__(SEL_NT) scl_select_kernel(const float* __restrict__ dist, int64_t n, uint32_t T,
-                                                            uint32_t* __restrict__ kappa)
+__global__ void __launch_bounds__(SEL_NT) scl_select_kernel(const float* __restrict__ dist, int64_t n, int64_t ldn,
+                                                            uint32_t T, uint32_t* __restrict__ kappa)
 {
     __shared__ uint32_t hist[2048];
     __shared__ uint32_t wtmp[SEL_NT / 32 + 4];
-    const uint32_t* v = reinterpret_cast<const uint32_t*>(dist) + (int64_t)blockIdx.x * n;
+    __shared__ uint32_t found;
+    const uint32_t* v = reinterpret_cast<const uint32_t*>(dist) + (int64_t)blockIdx.x * ldn;  // 16-byte aligned
     uint32_t prefix = 0, need = T, inbin = 0;
     const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
     for (int pass = 0; pass < 3; ++pass) {
@@ -208,10 +243,17 @@ __global__ void __launch_bounds__(SEL_NT) scl_select_kernel(const float* __restr
         for (int t = threadIdx.x; t < 2048; t += SEL_NT) hist[t] = 0u;
         __syncthreads();
         const uint32_t want = hi >= 32 ? 0u : prefix >> hi;
-        for (int64_t p0 = 0; p0 < n; p0 += SEL_NT) {  // block-uniform trip count: hist_add takes whole warps
-            const int64_t p = p0 + threadIdx.x;
-            const uint32_t x = p < n ? v[p] : 0u;
-            hist_add(hist, (x >> sh) & (uint32_t)(nb - 1), p < n && (hi >= 32 ? 0u : x >> hi) == want);
+        // four consecutive values per thread (one 16-byte load); block-uniform
+        // trip count: hist_add takes whole warps
+        for (int64_t p0 = 0; p0 < n; p0 += 4 * SEL_NT) {
+            const int64_t p = p0 + 4 * threadIdx.x;
+            uint4 x4 = make_uint4(0u, 0u, 0u, 0u);
+            if (p < n) x4 = *reinterpret_cast<const uint4*>(v + p);  // p + 3 < ldn
+            const uint32_t xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                hist_add(hist, (xs[e] >> sh) & (uint32_t)(nb - 1),
+                         p + e < n && (hi >= 32 ? 0u : xs[e] >> hi) == want);
         }
         __syncthreads();
         uint32_t below;
@@ -219,39 +261,36 @@ __global__ void __launch_bounds__(SEL_NT) scl_select_kernel(const float* __restr
         prefix |= bin << sh;
         need -= below;
     }
-    // prefix = d*; need in [1, inbin] points at d* collide, the lowest ids first
+    // prefix = d*; need in [1, inbin] points at d* collide, the lowest ids first:
+    // a scan in id order, eight consecutive ids per thread per round
     uint32_t last = 0xffffffffu;
     if (need < inbin) {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
         uint32_t run = 0;
-        for (int64_t base = 0; base < n; base += SEL_NT) {
-            const int64_t p = base + threadIdx.x;
-            const bool tie = p < n && v[p] == prefix;
-            const uint32_t bal = __ballot_sync(0xffffffffu, tie);
-            if (lane == 0) wtmp[w] = __popc(bal);
-            __syncthreads();
-            if (w == 0) {
-                const uint32_t c = lane < SEL_NT / 32 ? wtmp[lane] : 0u;
-                uint32_t inc = c;
+        for (int64_t base = 0; base < n; base += 8 * SEL_NT) {  // block-uniform
+            const int64_t p = base + 8 * threadIdx.x;
+            uint32_t xs[8];
+            uint4 a4 = make_uint4(0u, 0u, 0u, 0u), b4 = a4;
+            if (p < n) a4 = *reinterpret_cast<const uint4*>(v + p);          // p + 3 < ldn
+            if (p + 4 < n) b4 = *reinterpret_cast<const uint4*>(v + p + 4);  // p + 7 < ldn
+            xs[0] = a4.x; xs[1] = a4.y; xs[2] = a4.z; xs[3] = a4.w;
+            xs[4] = b4.x; xs[5] = b4.y; xs[6] = b4.z; xs[7] = b4.w;
+            uint32_t c = 0;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
-                }
-                wtmp[lane] = inc - c;
-                if (lane == 31) wtmp[SEL_NT / 32] = inc;
+            for (int e = 0; e < 8; ++e) c += (p + e < n && xs[e] == prefix) ? 1u : 0u;
+            uint32_t tot;
+            const uint32_t ex = block_scan_pairs_1024(c, wtmp, &tot);
+            if (run + ex < need && run + ex + c >= need) {  // the need-th tie is among this thread's eight
+                uint32_t r = run + ex;
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (p + e < n && xs[e] == prefix && ++r == need) found = (uint32_t)(p + e);
             }
             __syncthreads();
-            const uint32_t rank = run + wtmp[w] + __popc(bal & ((1u << lane) - 1u));  // ties before this point
-            if (tie && rank + 1 == need) wtmp[SEL_NT / 32 + 1] = (uint32_t)p;
-            const uint32_t total = wtmp[SEL_NT / 32];
-            __syncthreads();
-            if (run + total >= need) {
-                last = wtmp[SEL_NT / 32 + 1];
+            if (run + tot >= need) {
+                last = found;
                 break;
             }
-            run += total;
-            __syncthreads();
+            run += tot;
         }
     }
     if (threadIdx.x == 0) {
@@ -261,7 +300,8 @@ __global__ void __launch_bounds__(SEL_NT) scl_select_kernel(const float* __restr
 }
 
 // 3. SC-scores and each query's score histogram: grid (point blocks, B)
-__global__ void __launch_bounds__(256) scl_score_kernel(const float* __restrict__ dist, int64_t n, int32_t Ns,
+__global__ void __launch_bounds__(256) scl_score_kernel(const float* __restrict__ dist, int64_t n, int64_t ldn,
+                                                        int32_t Ns,
                                                         const uint32_t* __restrict__ kappa, uint8_t* __restrict__ score,
                                                         uint32_t* __restrict__ shist)
 {
@@ -269,13 +309,13 @@ __global__ void __launch_bounds__(256) scl_score_kernel(const float* __restrict_
     const int64_t b = blockIdx.y;
     if (threadIdx.x < 64) h[threadIdx.x] = 0u;
     __syncthreads();
-    const uint32_t* v = reinterpret_cast<const uint32_t*>(dist) + b * Ns * n;
+    const uint32_t* v = reinterpret_cast<const uint32_t*>(dist) + b * Ns * ldn;
     for (int64_t p0 = (int64_t)blockIdx.x * 256; p0 < n; p0 += (int64_t)gridDim.x * 256) {
         const int64_t p = p0 + threadIdx.x;  // block-uniform trip count: hist_add takes whole warps
         uint32_t sc = 0;
         if (p < n) {
             for (int i = 0; i < Ns; ++i) {
-                const uint32_t x = v[(int64_t)i * n + p];
+                const uint32_t x = v[(int64_t)i * ldn + p];
                 const uint32_t ds = kappa[2 * (b * Ns + i)], last = kappa[2 * (b * Ns + i) + 1];
                 sc += (x < ds || (x == ds && (uint32_t)p <= last)) ? 1u : 0u;
             }
@@ -514,7 +554,7 @@ int sc_linear_chunk(const DeviceIndex* ix, const float* Q, int64_t bq, uint32_t 
                     const SclLayout& L, char* ws, int32_t* ids, float* dist_out, uint8_t* dbg_scores,
                     int32_t* dbg_cands, cudaStream_t st)
 {
-    const int64_t n = ix->n, ntile = (n + SCL_TILE - 1) / SCL_TILE;
+    const int64_t n = ix->n, ntile = (n + SCL_TILE - 1) / SCL_TILE, ldn = (n + 3) & ~int64_t(3);
     const int Ns = ix->Ns;
     float* dist = reinterpret_cast<float*>(ws + L.o_dist);
     uint32_t* kappa = reinterpret_cast<uint32_t*>(ws + L.o_kappa);
@@ -525,17 +565,17 @@ int sc_linear_chunk(const DeviceIndex* ix, const float* Q, int64_t bq, uint32_t 
     int32_t* cands = reinterpret_cast<int32_t*>(ws + L.o_cands);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + L.o_keys);
     const int maxlen = ix->d - (Ns - 1) * ix->sub_s;
-    const size_t dsmem = (size_t)SCL_QT * maxlen * 4;
+    const size_t dsmem = (size_t)SCL_QT * ((maxlen + 3) & ~3) * 4;
     if (dsmem > 48 * 1024)
         SUCO_CUDA_TRY(cudaFuncSetAttribute(scl_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
     scl_dist_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)((bq + SCL_QT - 1) / SCL_QT)), 256, dsmem, st>>>(
-        ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, Q, bq, dist, ix->dperm, ix->metric);
+        ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, Q, bq, dist, ldn, ix->dperm, ix->metric);
     SUCO_LAUNCH_CHECK("scl_dist_kernel");
-    scl_select_kernel<<<(unsigned)(bq * Ns), SEL_NT, 0, st>>>(dist, n, T, kappa);
+    scl_select_kernel<<<(unsigned)(bq * Ns), SEL_NT, 0, st>>>(dist, n, ldn, T, kappa);
     SUCO_LAUNCH_CHECK("scl_select_kernel");
     SUCO_CUDA_TRY(cudaMemsetAsync(shist, 0, (size_t)bq * 64 * 4, st));
     const unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
-    scl_score_kernel<<<dim3(gx, (unsigned)bq), 256, 0, st>>>(dist, n, Ns, kappa, score, shist);
+    scl_score_kernel<<<dim3(gx, (unsigned)bq), 256, 0, st>>>(dist, n, ldn, Ns, kappa, score, shist);
     SUCO_LAUNCH_CHECK("scl_score_kernel");
     scl_cut_kernel<<<(unsigned)bq, 32, 0, st>>>(shist, Ns, (uint32_t)C, cut);
     SUCO_LAUNCH_CHECK("scl_cut_kernel");
@@ -545,6 +585,9 @@ int sc_linear_chunk(const DeviceIndex* ix, const float* Q, int64_t bq, uint32_t 
     SUCO_LAUNCH_CHECK("scl_scan_kernel");
     scl_compact_kernel<<<dim3((unsigned)ntile, (unsigned)bq), 256, 0, st>>>(score, n, cut, tcnt, C, cands);
     SUCO_LAUNCH_CHECK("scl_compact_kernel");
+    if ((size_t)ix->ld * 4 > 48 * 1024)
+        SUCO_CUDA_TRY(cudaFuncSetAttribute(scl_rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(ix->ld * 4)));
     scl_rerank_kernel<<<(unsigned)bq, RR_NT, (size_t)ix->ld * 4, st>>>(ix->X, ix->ld, Q, ix->d, cands, C, k, keys,
                                                                        ids, dist_out, ix->dperm, ix->metric);
     SUCO_LAUNCH_CHECK("scl_rerank_kernel");
@@ -564,7 +607,9 @@ int sc_linear_checks(const suco_index* index, int32_t k, double alpha, double be
     const DeviceIndex& ix = index->ix;
     if (ix.Ns > 63) return fail(SUCO_EUNSUPPORTED, "SC-Linear scores need Ns < 64");
     const int maxlen = ix.d - (ix.Ns - 1) * ix.sub_s;
-    if ((size_t)SCL_QT * maxlen * 4 > 200 * 1024)
+    if ((size_t)ix.ld * 4 > 200 * 1024)
+        return fail(SUCO_EUNSUPPORTED, "SC-Linear stages a query of %d dims in shared memory: too long", ix.d);
+    if ((size_t)SCL_QT * ((maxlen + 3) & ~3) * 4 > 200 * 1024)
         return fail(SUCO_EUNSUPPORTED, "SC-Linear stages %d query slices of %d dims in shared memory: too long", SCL_QT,
                     maxlen);
     return SUCO_OK;
