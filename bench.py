@@ -38,6 +38,9 @@ sys.path.insert(0, ROOT)
 from paper_2411_14754_gb300 import replicas  # noqa: E402 (which batches a rank answers, timing reduction)
 
 METRIC = "QPS at recall@10>=0.95 on 1 GB300, learned-alpha/BF16 vs plain FP32; % HBM peak"
+# the side lines (fixed operating points, SC-Linear) do not target a recall
+METRIC_FIXED = "QPS at a fixed alpha/beta on 1 GB300 (recall reported, not targeted); % HBM peak"
+METRIC_SCL = "QPS of SC-Linear (Algorithm 1, no index) at a fixed alpha/beta on 1 GB300"
 UNIT = "queries/s"
 
 
@@ -65,6 +68,8 @@ def parse():
                    help="cheapest margin pairs (by modelled bytes) timed for the learned arm")
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
                    help="re-rank precision of the fixed-ratio path")
+    p.add_argument("--label-mode", default="full", choices=["full", "lagrange"],
+                   help="per-query training labels of the ratio network (learn.labels_from_recalls)")
     p.add_argument("--sc-linear", action="store_true", help="time SC-Linear (Algorithm 1, no index) instead")
     p.add_argument("--build", action="store_true", help="time the index build (Algorithm 2) instead")
     p.add_argument("--rank-precision", default="fp32", choices=["fp32", "bf16", "fp8"],
@@ -383,7 +388,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     n_train = args.n_train or w.n_train
     t0 = time.time()
     Qt = torch.from_numpy(W.queries(w.number, nq=n_train, train=True)).to(dev)
-    model, rep = L.fit(index, Xd, Qt, w.k, target=args.target_recall, log=note)
+    model, rep = L.fit(index, Xd, Qt, w.k, target=args.target_recall, log=note, label_mode=args.label_mode)
     del Qt
     train_s = time.time() - t0
     note(f"trained: {json.dumps(rep)}")
@@ -576,7 +581,7 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     if rank == 0:
         cfg = workload_config(w)
         method = {"arm": "learned per-query alpha/beta", "network": f"MLP {3 * w.Ns}-{model.H}-2, GELU, BF16 weights",
-                  "n_train": n_train, "rerank": ("FP32" if learned_prec == "fp32" else
+                  "n_train": n_train, "labels": args.label_mode, "rerank": ("FP32" if learned_prec == "fp32" else
                                                  f"{learned_prec.upper()} coarse + exact FP32 top {R}"),
                   "selection": (f"margins and precision chosen on the {Qv.shape[0]} validation queries of the training "
                                 f"set at recall >= {sel_target:.3f}; recall_at_k measured on the {w.nq} evaluation "
@@ -725,7 +730,7 @@ def run_batching(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
         method = {"arm": (f"beta={w.beta}, per-query k in {list(w.k_mix)} and alpha in {list(w.alpha_mix)} drawn "
                           f"uniformly, FP32")}
         cfg["launch"] = {"cluster_size": shape[0], "threads": shape[1], "cuda_graphs": True, "persistent": True}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC_FIXED, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": mean_launch_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
                 "method": method,
@@ -778,7 +783,7 @@ def run_sc_linear(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     peak = 152 * 128 * 2.07e9 / 1e12
     achieved = 2.0 * w.n * w.d * B / (total_ms / args.steps / 1000.0) / 1e12
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC_SCL, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(w, B),
@@ -1021,7 +1026,7 @@ def main():
         cfg = workload_config(w, B)
         method = {"arm": f"fixed alpha={w.alpha}, beta={w.beta}", "rerank": args.precision,
                   "exact_rerank": args.exact_rerank, "cell_ranking": args.rank_precision}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC_FIXED, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "method": method, "recall_at_k": rec, "k": w.k,

@@ -87,7 +87,8 @@ def labels_from_recalls(rec, n, d, Ns, alphas=ALPHA_GRID, betas=BETA_GRID, mode=
     """Per-query (log alpha, log beta) labels from grid recalls rec[q, ia, ib].
 
     mode "full": the cheapest grid point at which the query's recall is 1 (the
-    largest point when none is).
+    largest point when none is); at k = 10 that is the cheapest point where the
+    query alone passes a 0.95 recall target.
     mode "lagrange": the point maximising recall - lam * bytes for one common
     lam >= 0, the largest lam whose mean recall over the queries still reaches
     the target (bisection); a query then gets more bytes only where they buy
@@ -289,7 +290,7 @@ def cheapest_fixed(rec_mean, n, d, Ns, target=0.95, alphas=ALPHA_GRID, betas=BET
 
 def fit(index: S.SucoIndex, Xd: torch.Tensor, Qtrain: torch.Tensor, k: int, val_frac: float = 0.1,
         target: float = 0.95, hidden: int = 256, epochs: int = 30, batch: int = 1024, lr: float = 3e-3,
-        seed: int = 0, gt=None, log=None, label_mode: str = "lagrange", label_target: float = 0.96):
+        seed: int = 0, gt=None, log=None, label_mode: str = "full", label_target: float = 0.96):
     """Whole training recipe on one index: exact k-NN of the training queries,
     grid labels from the plain path, network training on the GPU, then the
     margin that brings the validation split to the target mean recall@k.
