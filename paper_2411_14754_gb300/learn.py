@@ -22,8 +22,8 @@ import torch
 
 from . import suco as S
 
-ALPHA_GRID = (0.01, 0.02, 0.03, 0.05, 0.08, 0.12, 0.2)
-BETA_GRID = (0.001, 0.002, 0.003, 0.005, 0.008, 0.016)
+ALPHA_GRID = (0.005, 0.01, 0.02, 0.03, 0.05, 0.08, 0.12, 0.2)
+BETA_GRID = (0.0005, 0.001, 0.002, 0.003, 0.005, 0.008, 0.016)
 FALLBACK = (0.05, 0.005)
 # clamps of the predicted ratios; the beta bound also sizes the query kernel's
 # candidate slots (shared memory), so it stays at the grid's largest beta

@@ -25,8 +25,11 @@ def _cells_from_csr(off, perm, n, K):
     return cell
 
 
-@pytest.mark.parametrize("n,d,Ns,sk", [(10_000, 128, 8, 10), (1001, 13, 3, 5), (4000, 64, 16, 33), (300, 8, 2, 20)])
+@pytest.mark.parametrize("n,d,Ns,sk", [(10_000, 128, 8, 10), (1001, 13, 3, 5), (4000, 64, 16, 33), (300, 8, 2, 20),
+                                      (100, 4, 1, 10), (70_000, 8, 1, 256), (2048 * 3 + 1, 16, 2, 17)])
 def test_imi_from_assignments_is_bit_exact(n, d, Ns, sk):
+    # one radix pass for K <= 256, two above it (K = 65536 uses both digits
+    # whole); tiles of 2048 keys, whole and ragged
     X = W.random_data(n + d, n, d)
     rng = np.random.default_rng(n)
     assign = rng.integers(0, sk, size=(Ns, 2, n)).astype(np.int32)
@@ -73,6 +76,34 @@ def test_kmeans_one_iteration_matches_oracle():
                 assert abs(dd[p, got[p]] - dd[p, best[p]]) <= 1e-5 * max(dd[p, best[p]], 1.0)
             mism += len(bad)
     assert mism <= 10
+
+
+@pytest.mark.parametrize("d,Ns,metric", [(13, 2, "l2"), (48, 2, "l2"), (50, 2, "l2"), (120, 2, "l2"), (80, 1, "l2"),
+                                         (50, 2, "l1"), (120, 2, "l1"), (80, 1, "l1")])
+def test_kmeans_iteration_matches_oracle_for_each_half_length(d, Ns, metric):
+    # halves of 3-4 dims (the assignment kernel's 8-wide rows), 12-13 (16-wide),
+    # 30 (32-wide) and 40 (the any-length kernel), under both metrics: one
+    # Lloyd iteration from given points, then the final assignment
+    n, sk = 3000, 8
+    X = W.random_data(7 + d, n, d)
+    rng = np.random.default_rng(d)
+    init = np.stack([np.stack([rng.choice(n, sk, replace=False) for _ in range(2)]) for _ in range(Ns)])
+    m = oracle.METRIC_L1 if metric == "l1" else 0
+    ix = pkg.suco_build_index(torch.from_numpy(X).cuda(), Ns, sk, 1, init_ids=init, metric=metric)
+    ex = pkg.suco_export_index(ix)
+    pkg.suco_free(ix)
+    ref = oracle.build_index(X, Ns, sk, 1, init, metric=m)
+    kind = "cityblock" if m else "sqeuclidean"
+    for i in range(Ns):
+        cell = _cells_from_csr(ex["cell_off"][i].astype(np.int64), ex["perm"][i], n, sk * sk)
+        for h in range(2):
+            off, ln = oracle.half_dims(d, Ns, i, h)
+            g = ex["centroids"][i, h, :, :ln].astype(np.float64)
+            np.testing.assert_allclose(g, ref["centroids"][i, h, :, :ln], rtol=1e-5, atol=1e-5)
+            dd = cdist(X[:, off:off + ln].astype(np.float64), g, kind)
+            got = cell // sk if h == 0 else cell % sk
+            best = dd.min(axis=1)
+            np.testing.assert_allclose(dd[np.arange(n), got], best, rtol=1e-5, atol=1e-6)
 
 
 def test_kmeans_converges_on_separated_blobs():
