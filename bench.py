@@ -103,9 +103,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(workload):
+def committed_traffic(workload, operating_point=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current kernel source (and, where given, at the same operating-point
+    setup); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(path))
@@ -114,7 +115,16 @@ def committed_traffic(workload):
     e = t.get(str(workload))
     if not e or e.get("kernel_source_hash") != kernel_source_hash():
         return None
+    if operating_point is not None and e.get("operating_point") != operating_point:
+        return None
     return e.get("dram_bytes_per_launch")
+
+
+def learned_setup(L, label_mode, margin):
+    """What decides the learned arm's operating points: the label grid and
+    mode and the chosen margins (a traffic record holds for these only)."""
+    return {"labels": label_mode, "alpha_grid": list(L.ALPHA_GRID), "beta_grid": list(L.BETA_GRID),
+            "margin": [float(m) for m in margin]}
 
 
 class ClockSampler:
@@ -563,7 +573,8 @@ def run_learned(args, torch, tdist, pkg, W, rank, local_rank, world, dev):
     hbm = hbm or 6800.0
     achieved = bytes_steps / args.steps / (query_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": committed_traffic(f"{w.number}-learned") if learned_prec == "fp32" else None,
+                "traffic": (committed_traffic(f"{w.number}-learned", learned_setup(L, args.label_mode, margin))
+                            if learned_prec == "fp32" else None),
                 "peak_source": peak_src,
                 "kernel": f"suco_query_kernel (learned per-query alpha/beta, {learned_prec} re-rank, one launch per batch)",
                 "algorithmic_bytes_per_query": bytes_steps / sum(nq_step), "mean_launch_ms": query_ms}
