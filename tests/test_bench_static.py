@@ -35,3 +35,27 @@ def test_bench_json_keys_are_present_in_every_arm():
                 '"cpu_baseline"', '"e2e"', '"clocks"', '"gpu_launches"'):
         # the learned arm, the batching arm and the fixed-ratio arm each print one line
         assert src.count(key) >= 3, key
+
+
+def test_committed_traffic_needs_the_same_source_and_operating_point(tmp_path, monkeypatch):
+    # a DRAM-traffic record counts only for the kernel source it was taken on
+    # and, for the learned arm, the label setup and margins it was taken at
+    import json
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2411_14754_gb300 import learn as L
+    setup = bench.learned_setup(L, "full", (0.75, 0.75))
+    assert setup["alpha_grid"] == list(L.ALPHA_GRID) and setup["margin"] == [0.75, 0.75]
+    rec = {"5-learned": {"kernel_source_hash": bench.kernel_source_hash(), "dram_bytes_per_launch": 123.0,
+                         "operating_point": setup},
+           "5": {"kernel_source_hash": "0" * 16, "dram_bytes_per_launch": 7.0}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["5-learned"]["kernel_source_hash"])
+    assert bench.committed_traffic("5-learned", setup) == 123.0
+    assert bench.committed_traffic("5-learned", bench.learned_setup(L, "full", (0.5, 0.75))) is None
+    assert bench.committed_traffic("5-learned", bench.learned_setup(L, "lagrange", (0.75, 0.75))) is None
+    assert bench.committed_traffic("5") is None          # taken on another source
+    assert bench.committed_traffic("missing") is None
