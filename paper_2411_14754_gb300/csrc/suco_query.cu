@@ -122,6 +122,7 @@ struct QArgs {
     uint32_t o_qn;        // the next query's row, copied in while S6 runs
     uint32_t s3_stride;   // bytes of one S3 scratch group in the union region
     uint32_t pair_ok;     // 1: a CTA that owns two subspaces ranks them at once, one per half
+    uint32_t o_bkt;       // nonzero: S3 keeps every cell's value bucket (u16) at o_union + group + o_bkt
 };
 
 // ---------------------------------------------------------------------------
@@ -553,7 +554,26 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     if (tid == 0) *mcount = 0u;
     if (co_s) cp_async_wait_all();
     group_sync<NT>(bar);
-    if (c_of < sk) {
+    // with a bucket store, cells in flat order x = a * sqrtK + c (thread tid
+    // takes x = tid, tid + NT, ..., stepping (a, c) without a division) and
+    // each cell's bucket kept for the member search; else the 2-D mapping
+    uint16_t* bkt = A.o_bkt ? reinterpret_cast<uint16_t*>(smem + A.o_union + grp * A.s3_stride + A.o_bkt) : nullptr;
+    const int K = sk * sk, step_a = NT / sk, step_c = NT - step_a * sk;
+    if (bkt) {
+        int a = tid / sk, c = tid - a * sk;
+        for (int x = tid; x < K; x += NT) {
+            const int bk = value_bucket(__fadd_rn(tb.d1[a], tb.d2[c]), smin, scale);
+            bkt[x] = (uint16_t)bk;
+            const uint32_t w = cell_size((uint32_t)x);
+            if (w) atomicAdd(&hist[bk], w);
+            a += step_a;
+            c += step_c;
+            if (c >= sk) {
+                c -= sk;
+                ++a;
+            }
+        }
+    } else if (c_of < sk) {
         const float d2c = tb.d2[c_of];
         for (int a = a_of; a < sk; a += a_step) {
             const uint32_t x = (uint32_t)(a * sk + c_of);
@@ -588,7 +608,29 @@ __device__ void rank_subspace(const QArgs& A, char* smem, int64_t b, int i, uint
     const int bstar = (int)bc[3];
     unsigned long long below = bc[4];
     // members of the crossing bucket (non-empty cells only)
-    if (c_of < sk) {
+    if (bkt) {
+        int a = tid / sk, c = tid - a * sk;
+        for (int x = tid; x < K; x += NT) {
+            if (bkt[x] == (uint16_t)bstar) {
+                const uint32_t w = cell_size((uint32_t)x);
+                if (w) {
+                    const float s = __fadd_rn(tb.d1[a], tb.d2[c]);
+                    const uint32_t slot = atomicAdd(mcount, 1u);
+                    if (slot < MCAP) {
+                        mkey[slot] = ((unsigned long long)__float_as_uint(s) << 16) | ((uint32_t)tb.r1[a] << 8) |
+                                     (uint32_t)tb.r2[c];
+                        mw[slot] = w;
+                    }
+                }
+            }
+            a += step_a;
+            c += step_c;
+            if (c >= sk) {
+                c -= sk;
+                ++a;
+            }
+        }
+    } else if (c_of < sk) {
         const float d2c = tb.d2[c_of];
         const uint32_t r2c = tb.r2[c_of];
         for (int a = a_of; a < sk; a += a_step) {
@@ -2070,6 +2112,14 @@ int layout_once(const DeviceIndex* ix, int CL, int npass, int nsmax, int NT, uin
     // has a thread for every centroid column (the 2-D cell mapping of S3)
     A.s3_stride = align16(s3_bytes + (A.o_cells ? cells_bytes : 0));
     A.pair_ok = (pair && 2ull * A.s3_stride <= ubytes && (uint32_t)(NT / 2) >= next_pow2((uint32_t)sk)) ? 1u : 0u;
+    // S3's per-cell bucket store, where the groups still fit the region with it
+    {
+        const uint64_t with = align16(A.s3_stride + 2ull * ix->K);
+        if ((A.pair_ok ? 2ull : 1ull) * with <= ubytes) {
+            A.o_bkt = (uint32_t)A.s3_stride;
+            A.s3_stride = (uint32_t)with;
+        }
+    }
     A.o_keys = (uint32_t)(o + ubytes - keys_bytes);
 
     o = align16(o + ubytes);
