@@ -39,7 +39,6 @@ namespace {
 
 constexpr int SCL_TILE = 4096;     // ids per compaction tile
 constexpr int SCL_QT = 32;         // queries per distance block
-constexpr int SCL_DC = 8;          // dimensions per register chunk of the distance kernel
 
 struct SclLayout {
     int64_t B = 0;                 // queries per batch
@@ -75,55 +74,83 @@ SclLayout scl_layout(const DeviceIndex* ix, int64_t B, int64_t C)
     return L;
 }
 
+// Two FP32 lanes in one 64-bit register: element-wise subtract, fused
+// multiply-add and add, each rounded to nearest even like the scalar
+// operation; |x| of both lanes by clearing the sign bits.
+__device__ __forceinline__ unsigned long long p2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long p2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long p2_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 // 1. distances.  Block: 256 points x SCL_QT queries (grid.y picks the query
 // group); per subspace the group's query slices are staged in shared memory
-// and every thread keeps one accumulator per query.
+// dimension-major ([j][query], zero for missing queries), and every thread
+// keeps one accumulator per query, two queries per 64-bit register: for each
+// dimension in order it forms (x_j, x_j) once and updates the pairs with
+// sub.f32x2 and fma.f32x2 (or the absolute value and add.f32x2 for L1).
+// Each lane of a pair sees the scalar operations in the scalar order, so the
+// distances are bit-identical to a one-query-at-a-time loop.
+template <int MET>
 __global__ void __launch_bounds__(256, 2) scl_dist_kernel(const float* __restrict__ X, int64_t ld, int64_t n, int32_t d,
                                                        int32_t Ns, int32_t sub_s, const float* __restrict__ Q, int64_t nq,
                                                        float* __restrict__ dist, int64_t ldn,
-                                                       const int32_t* __restrict__ qperm, int metric)
+                                                       const int32_t* __restrict__ qperm)
 {
-    extern __shared__ __align__(16) float qs[];  // [SCL_QT][lq]: rows padded to 4 floats (16-byte loads)
+    constexpr int NP = SCL_QT / 2;               // query pairs
+    extern __shared__ __align__(16) float qs[];  // [maxlen][SCL_QT]
     const int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int64_t q0 = (int64_t)blockIdx.y * SCL_QT;
     const int nqg = (int)(nq - q0 < SCL_QT ? nq - q0 : SCL_QT);
     for (int i = 0; i < Ns; ++i) {
         const int off = i * sub_s, len = (i == Ns - 1) ? d - (Ns - 1) * sub_s : sub_s;
-        const int lq = (len + 3) & ~3;
         __syncthreads();
-        for (int t = threadIdx.x; t < nqg * len; t += 256) {
-            const int qq = t / len, j = t - qq * len;
-            qs[qq * lq + j] = query_col(Q + (q0 + qq) * d, qperm, off + j);
+        for (int t = threadIdx.x; t < SCL_QT * len; t += 256) {
+            const int j = t / SCL_QT, qq = t - j * SCL_QT;
+            qs[t] = qq < nqg ? query_col(Q + (q0 + qq) * d, qperm, off + j) : 0.f;
         }
         __syncthreads();
         if (p >= n) continue;
-        float acc[SCL_QT];
+        unsigned long long acc[NP];
 #pragma unroll
-        for (int qq = 0; qq < SCL_QT; ++qq) acc[qq] = 0.f;
+        for (int m = 0; m < NP; ++m) acc[m] = 0ull;  // (+0, +0)
         const float* xr = X + p * ld + off;
-        for (int j0 = 0; j0 < len; j0 += SCL_DC) {
-            float xv[SCL_DC];
+        const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qs);
+        for (int j = 0; j < len; ++j) {
+            const unsigned u = __float_as_uint(__ldg(xr + j));
+            const unsigned long long xx = (unsigned long long)u | ((unsigned long long)u << 32);
 #pragma unroll
-            for (int u = 0; u < SCL_DC; ++u) xv[u] = j0 + u < len ? __ldg(xr + j0 + u) : 0.f;
-#pragma unroll
-            for (int qq = 0; qq < SCL_QT; ++qq) {
-                if (qq < nqg) {
-                    const float4 qa = *reinterpret_cast<const float4*>(qs + qq * lq + j0);  // j0 % 8 == 0
-                    const float4 qb = j0 + 4 < lq ? *reinterpret_cast<const float4*>(qs + qq * lq + j0 + 4) : qa;
-                    const float qv[SCL_DC] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-#pragma unroll
-                    for (int u = 0; u < SCL_DC; ++u)
-                        if (j0 + u < len) {
-                            const float df = __fsub_rn(xv[u], qv[u]);
-                            acc[qq] = metric == SUCO_METRIC_L1 ? __fadd_rn(acc[qq], fabsf(df))
-                                                               : __fmaf_rn(df, df, acc[qq]);
-                        }
+            for (int m = 0; m < NP; m += 2) {
+                const ulonglong2 qv = q2[j * (NP / 2) + m / 2];  // queries 2m .. 2m+3 of dimension j
+                const unsigned long long d0 = p2_sub(xx, qv.x), d1 = p2_sub(xx, qv.y);
+                if constexpr (MET == SUCO_METRIC_L1) {
+                    acc[m] = p2_add(acc[m], d0 & 0x7fffffff7fffffffull);
+                    acc[m + 1] = p2_add(acc[m + 1], d1 & 0x7fffffff7fffffffull);
+                } else {
+                    acc[m] = p2_fma(d0, d0, acc[m]);
+                    acc[m + 1] = p2_fma(d1, d1, acc[m + 1]);
                 }
             }
         }
 #pragma unroll
-        for (int qq = 0; qq < SCL_QT; ++qq)
-            if (qq < nqg) dist[((q0 + qq) * Ns + i) * ldn + p] = acc[qq];
+        for (int m = 0; m < NP; ++m) {
+            const int qa = 2 * m, qb = 2 * m + 1;
+            if (qa < nqg) dist[((q0 + qa) * Ns + i) * ldn + p] = __uint_as_float((unsigned)acc[m]);
+            if (qb < nqg) dist[((q0 + qb) * Ns + i) * ldn + p] = __uint_as_float((unsigned)(acc[m] >> 32));
+        }
     }
 }
 
@@ -565,11 +592,21 @@ int sc_linear_chunk(const DeviceIndex* ix, const float* Q, int64_t bq, uint32_t 
     int32_t* cands = reinterpret_cast<int32_t*>(ws + L.o_cands);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + L.o_keys);
     const int maxlen = ix->d - (Ns - 1) * ix->sub_s;
-    const size_t dsmem = (size_t)SCL_QT * ((maxlen + 3) & ~3) * 4;
-    if (dsmem > 48 * 1024)
-        SUCO_CUDA_TRY(cudaFuncSetAttribute(scl_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-    scl_dist_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)((bq + SCL_QT - 1) / SCL_QT)), 256, dsmem, st>>>(
-        ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, Q, bq, dist, ldn, ix->dperm, ix->metric);
+    const size_t dsmem = (size_t)SCL_QT * maxlen * 4;
+    const dim3 dgrid((unsigned)((n + 255) / 256), (unsigned)((bq + SCL_QT - 1) / SCL_QT));
+    if (ix->metric == SUCO_METRIC_L1) {
+        if (dsmem > 48 * 1024)
+            SUCO_CUDA_TRY(cudaFuncSetAttribute(scl_dist_kernel<SUCO_METRIC_L1>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+        scl_dist_kernel<SUCO_METRIC_L1><<<dgrid, 256, dsmem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, Q, bq, dist,
+                                                                  ldn, ix->dperm);
+    } else {
+        if (dsmem > 48 * 1024)
+            SUCO_CUDA_TRY(cudaFuncSetAttribute(scl_dist_kernel<SUCO_METRIC_L2>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+        scl_dist_kernel<SUCO_METRIC_L2><<<dgrid, 256, dsmem, st>>>(ix->X, ix->ld, n, ix->d, Ns, ix->sub_s, Q, bq, dist,
+                                                                  ldn, ix->dperm);
+    }
     SUCO_LAUNCH_CHECK("scl_dist_kernel");
     scl_select_kernel<<<(unsigned)(bq * Ns), SEL_NT, 0, st>>>(dist, n, ldn, T, kappa);
     SUCO_LAUNCH_CHECK("scl_select_kernel");
@@ -609,7 +646,7 @@ int sc_linear_checks(const suco_index* index, int32_t k, double alpha, double be
     const int maxlen = ix.d - (ix.Ns - 1) * ix.sub_s;
     if ((size_t)ix.ld * 4 > 200 * 1024)
         return fail(SUCO_EUNSUPPORTED, "SC-Linear stages a query of %d dims in shared memory: too long", ix.d);
-    if ((size_t)SCL_QT * ((maxlen + 3) & ~3) * 4 > 200 * 1024)
+    if ((size_t)SCL_QT * maxlen * 4 > 200 * 1024)
         return fail(SUCO_EUNSUPPORTED, "SC-Linear stages %d query slices of %d dims in shared memory: too long", SCL_QT,
                     maxlen);
     return SUCO_OK;
